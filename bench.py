@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-solution of the mixed-precision BS3 solve at a fixed
+global error, against the binary64 GPU path, on Kuramoto N = 4096,
+K_ij = (2/N)(1 + U(-1/2, 1/2)), omega ~ N(0,1), theta0 ~ U(0, 2 pi),
+t in [0, 50] (seeded synthetic data; the paper's Sobol test suites are not
+available).
+
+A step is one complete adaptive solve (every attempt: three coupling
+evaluations, stage combinations, the embedded error norm and the controller)
+inside one persistent kernel.  Inputs are resident in HBM; the L2 is flushed
+between timed steps by a 512 MiB write outside the timed events.
+
+Default run: N = 1 GPU.  Under torchrun each rank solves an independent replica
+(other seed); the reported time is the maximum over ranks ("replicas only").
+``--impl reference`` times the CPU oracle instead (bounded sample, extrapolated).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_AGENTS = 4096
+T1 = 50.0
+RTOL = 1e-6
+ERROR_FACTOR = 2.0          # "fixed global error": within this factor of the binary64 GPU path
+METRIC = "time-to-solution at fixed global error, mixed vs FP64 GPU; coupling HBM GB/s"
+WORKLOAD = "kuramoto_N4096_t50"
+REF_FILE = os.path.join(ROOT, "tests", "golden", "ref_kuramoto_N4096_seed0_t50.npy")
+STORE_BYTES = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2, "fp8e4m3": 1}
+# (variant, stored weights) surveyed; the headline is the fastest mixed one whose
+# global error stays within ERROR_FACTOR of the binary64 path.
+CANDIDATES = [("double", "f64"), ("mixed2", "f32"), ("mixed1", "f32"), ("mixed2", "bf16"),
+              ("mixed1", "bf16"), ("mixed1", "f16"), ("single", "f32")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bs3", choices=["bs3", "reference"])
+    ap.add_argument("--accum", default="float2", choices=["float2", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-attempts", type=int, default=30)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def normalized_error(a, b, n):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / math.sqrt(n))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.device_index = device_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    bs3.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = workloads.kuramoto(N_AGENTS, seed=rank, t1=T1, rtol=RTOL)
+    n = w.N * w.d
+    systems = {}
+
+    def system(store):
+        if store not in systems:
+            s = bs3.System(w.kind, w.N, w.params, None, device=local, stream=stream.cuda_stream)
+            s.set_coupling(w.coupling, store)
+            systems[store] = s
+        return systems[store]
+
+    y0_d = torch.tensor(w.y0, dtype=torch.float64, device=dev)
+    y_d = torch.empty_like(y0_d)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def solve_dev(variant, store, rtol=RTOL):
+        s = system(store)
+        rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0_d, rtol, rtol, bs3.VARIANT_IDS[variant],
+                               bs3.ACCUM_IDS[args.accum], None, 0, None, y_d, 0)
+        if rc != bs3.OK:
+            raise RuntimeError(f"{variant}/{store}: {bs3.bs3_status_string(rc)}")
+        return st
+
+    def timed(variant, store, reps):
+        times, st = [], None
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solve_dev(variant, store)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, st, y_d.cpu().numpy()
+
+    # reference solution for the global error
+    if rank == 0 and os.path.exists(REF_FILE):
+        y_ref, ref_kind = np.load(REF_FILE), "oracle DOPRI5 rtol=atol=1e-12 (binary64 weights)"
+    else:
+        solve_dev("double", "f64", rtol=1e-11)
+        y_ref, ref_kind = y_d.cpu().numpy(), "GPU-derived: binary64 BS3 at rtol=atol=1e-11"
+
+    survey = {}
+    for variant, store in CANDIDATES:
+        solve_dev(variant, store)              # warm-up of this configuration
+        times, st, y = timed(variant, store, 2)
+        survey[f"{variant}/{store}"] = {
+            "ms": min(times), "accepted": st.n_accepted, "rejected": st.n_rejected,
+            "rhs_evals": st.n_rhs_evals, "global_error": normalized_error(y_ref, y, w.N)}
+    e_double = survey["double/f64"]["global_error"]
+    ok = [(v["ms"], k) for k, v in survey.items()
+          if not k.startswith("double") and v["global_error"] <= ERROR_FACTOR * e_double]
+    head = min(ok)[1] if ok else "mixed2/f32"
+    h_variant, h_store = head.split("/")
+
+    # ---------------------------------------------------------------- timed
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve_dev(h_variant, h_store)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solve_dev(h_variant, h_store)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    y_head = y_d.cpu().numpy()
+
+    # ---------------------------------------------------- end to end (host)
+    s = system(h_store)
+    y_host = np.empty(n)
+    e2e_ms = []
+    for _ in range(max(2, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st2 = bs3.bs3_solve(s.handle, w.t0, w.t1, w.y0, RTOL, RTOL, bs3.VARIANT_IDS[h_variant],
+                                bs3.ACCUM_IDS[args.accum], None, 0, None, y_host, bs3.HOST_IO)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        assert rc == bs3.OK
+
+    # --------------------------------------------------------------- roofline
+    evals = st.n_rhs_evals
+    bytes_per_eval = w.N * w.N * STORE_BYTES[h_store] + w.N * 4 * 2 + n * 8 * 6
+    achieved_gbs = evals * bytes_per_eval / (ms * 1e-3) / 1e9
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    result = {
+        "metric": METRIC,
+        "value": round(ms, 4),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "bf16", "f16": "f16", "f64": "f64", "fp8e4m3": "fp8"}[h_store]
+                 + "+f64" if h_variant != "single" else "f32",
+        "data": "synthetic (seeded numpy; Kuramoto shaped like the paper's Benchmark 2)",
+        "config": {"workload": WORKLOAD, "N": w.N, "t1": T1, "rtol": RTOL, "atol": RTOL,
+                   "variant": h_variant, "weights": h_store, "sigma_d_sum": args.accum,
+                   "parallelism": "replicas only" if world > 1 else "1 GPU",
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "reference_solution": ref_kind, "error_factor": ERROR_FACTOR},
+        "global_error": normalized_error(y_ref, y_head, w.N),
+        "fp64_gpu_ms": survey["double/f64"]["ms"],
+        "fp64_gpu_global_error": e_double,
+        "speedup_vs_fp64_gpu": survey["double/f64"]["ms"] / ms,
+        "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": evals,
+        "survey": survey,
+        "wall_s_timed_region": wall,
+        "clocks": clocks,
+        "e2e": {"value": round(statistics.median(e2e_ms), 4), "unit": "ms",
+                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + 64},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None,
+                     "note": "algorithmic bytes = rhs_evals x (N^2 b_K + vectors) per solve launch; "
+                             "peak of measured (MEASURED_PEAKS.json hbm_gbs); weights are L2-resident at N=4096"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, h_variant, h_store, st.n_accepted + st.n_rejected,
+                                              args.cpu_sample_attempts)
+    for s in systems.values():
+        s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_sample(w, variant, store, attempts):
+    from oracle import bs3 as obs3
+    from oracle import models
+    osys = models.from_workload(w, store)
+    t0 = time.perf_counter()
+    r = obs3.solve(osys, w.t0, w.t1, w.y0, w.rtol, w.atol, variant,
+                   limits=obs3.Limits(max_attempts=attempts))
+    dt = time.perf_counter() - t0
+    return dt, r.n_accepted + r.n_rejected
+
+
+def cpu_baseline(w, variant, store, gpu_attempts, sample_attempts):
+    dt, att = cpu_sample(w, variant, store, sample_attempts)
+    per = dt / max(att, 1)
+    return {"value": round(per * gpu_attempts * 1e3, 1), "unit": "ms", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"first {att} attempts of the same solve ({dt:.1f} s), per-attempt time "
+                      f"extrapolated to the GPU solve's {gpu_attempts} attempts; numpy/BLAS threads = cores"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workloads.kuramoto(N_AGENTS, seed=0, t1=T1, rtol=RTOL)
+    variant, store = "mixed1", "bf16"
+    sample = 6
+    for _ in range(args.warmup):
+        cpu_sample(w, variant, store, 2)
+    per = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        dt, att = cpu_sample(w, variant, store, sample)
+        per.append(dt / att)
+    wall = time.perf_counter() - t_all
+    attempts = 1442   # attempts of the full oracle solve of this workload at rtol 1e-6 (mixed1)
+    value = statistics.mean(per) * attempts * 1e3
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_AGENTS, "t1": T1, "rtol": RTOL,
+                                        "variant": variant, "weights": store},
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{sample} attempts per step, per-attempt time x {attempts} attempts"},
+        "e2e": {"value": round(value, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed_region": wall,
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,176 @@
+/*
+ * bs3.h -- C ABI of the GB300 (sm_103a) mixed-precision Bogacki-Shampine 3(2)
+ * solver for large ODE systems with dense, all-pairs, heterogeneous coupling.
+ *
+ * Method (paper: "Mixed-Precision in adaptive Runge-Kutta method for large ODE
+ * systems"):
+ *   - general model X_i' = F_i(X_i) + sum_j M_ij (.) G_ij(X_i, X_j)
+ *     (Sec. 2.1, Eq. General-Model) with three benchmark kinds (Eq. LCO,
+ *     Eq. Kuramoto, Eq. CC) plus the second-order oscillator form;
+ *   - the Bogacki-Shampine 3(2) pair with FSAL (Sec. 2.2, Table Butcher-O23,
+ *     Eq. Stage-ODE23), the embedded max-norm error (Eq. ERROR-O23), the
+ *     accept test E <= Rel and the failure conditions of Sec. 2.2;
+ *   - the precision distribution Single / Mixed1 / Mixed2 / Double of
+ *     Sec. 2.3, Table MP-Distrib, extended to bfloat16 / fp16 / fp8 storage of
+ *     the coupling weights (Sec. 4 names these formats as the next step).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a bs3_status code (0 = BS3_OK).  Nothing throws; on error
+ *     the outputs that could be produced are still written (see bs3_solve).
+ *   - State vectors are binary64, structure-of-arrays: component k of agent i
+ *     is y[k*N + i], length d*N with d = 2 (LCO_CFG, LCO_PAPER), 1 (KURAMOTO)
+ *     or 4 (CIRCADIAN).
+ *   - "Device pointer" means memory of the system's device (cudaMalloc or
+ *     managed); "host pointer" means ordinary or pinned host memory.
+ *   - The caller owns every pointer it passes; the library owns the system,
+ *     its stored (quantised) weights and all of its scratch buffers.
+ *   - Work is issued on the system's CUDA stream; bs3_solve and bs3_rhs
+ *     return after their results are complete.
+ *   - A system is not thread-safe: calls on one system must not overlap.
+ */
+#ifndef BS3_H
+#define BS3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bs3_system* bs3_system_t;
+
+/* Kinds of right-hand side (Sec. 2.1).
+ * BS3_LCO_CFG   second-order oscillators: x' = v, v' = -omega_i^2 x + sum_j A_ij x_j.
+ *               params[N] = omega_i.
+ * BS3_LCO_PAPER Eq. LCO: x' = v + sum_j M_ij (x_j - x_i), v' = -x.  n_params = 0.
+ * BS3_KURAMOTO  Eq. Kuramoto: theta' = omega_i + sum_j K_ij sin(theta_j - theta_i).
+ *               params[N] = omega_i.
+ * BS3_CIRCADIAN Eq. CC with Hill exponent 4, coupling on component 1:
+ *               pref_i sum_j W_ij atan(x_j1 - x_i1), pref_i = k0 Th_i a/(Th_i + x_i2^4),
+ *               Th_i = k1_i/(k0 - k1_i).  params[N + 8] = k1_i (N values), then
+ *               k0, k2, k3, a, b, c, eps, I0.  The coupling coefficient K of
+ *               the paper is folded into W. */
+typedef enum { BS3_LCO_CFG = 0, BS3_LCO_PAPER = 1, BS3_KURAMOTO = 2, BS3_CIRCADIAN = 3 } bs3_kind;
+
+/* Precision variants, Table MP-Distrib (Sec. 2.3): (F, Sigma, G) per stage.
+ * SINGLE: all S, state and stage combinations in binary32 (t, h, E in binary64).
+ * MIXED1: k2,k3 (S,S,S), k4 (D,D,S); MIXED2: k2..k4 (D,D,S); DOUBLE: all D. */
+typedef enum { BS3_SINGLE = 0, BS3_MIXED1 = 1, BS3_MIXED2 = 2, BS3_DOUBLE = 3 } bs3_variant;
+
+/* Element types of the coupling weights. */
+typedef enum { BS3_F64 = 0, BS3_F32 = 1, BS3_BF16 = 2, BS3_F16 = 3, BS3_FP8E4M3 = 4 } bs3_dtype;
+
+/* How a Sigma = D stage sums its binary32 products (G = S):
+ * BS3_ACC_F64    each product cast to binary64 and added in binary64 (Sec. 2.3, literal);
+ * BS3_ACC_FLOAT2 compensated float-float sum (TwoSum per product, about 44 bits);
+ * BS3_ACC_F32    plain binary32 sum (departs from the table; for study only).
+ * Sigma = S stages always sum in binary32; G = D stages in binary64. */
+typedef enum { BS3_ACC_F32 = 0, BS3_ACC_FLOAT2 = 1, BS3_ACC_F64 = 2 } bs3_accum;
+
+/* Status codes. */
+enum {
+    BS3_OK = 0,
+    BS3_ERR_INVALID_ARG = 1,
+    BS3_ERR_CUDA = 2,
+    BS3_ERR_MAX_STEPS = 3,        /* accepted + failed attempts reached I_max (Sec. 2.2) */
+    BS3_ERR_MAX_REJECTS = 4,      /* failed attempts above 0.85 I_max (Sec. 2.2) */
+    BS3_ERR_STEP_TOO_SMALL = 5,   /* h <= h_min = 100 eps_m (Sec. 2.2) */
+    BS3_ERR_TIMEOUT = 6,          /* wall-clock limits of Sec. 2.2 */
+    BS3_ERR_DEVICE_WAIT = 7,      /* a bounded device-side wait ran out */
+    BS3_ERR_NONFINITE = 8         /* NaN or Inf in the state, the stages or E */
+};
+
+/* Flags of bs3_solve. */
+enum {
+    BS3_HOST_IO = 1               /* y0, t_out and y_out are host pointers */
+};
+
+typedef struct {
+    int64_t n_accepted;           /* accepted attempts */
+    int64_t n_rejected;           /* failed attempts */
+    int64_t n_rhs_evals;          /* right-hand-side evaluations (2 + 3 per attempt) */
+    double  t_reached;            /* time of the last accepted state */
+    double  h_last;               /* step size the controller would use next */
+    int32_t status;               /* bs3_status of the solve */
+    int32_t n_out_written;        /* dense outputs written (t_out <= t_reached) */
+} bs3_stats;
+
+/* Failure conditions of Sec. 2.2 and the device wait bound. */
+typedef struct {
+    int64_t max_attempts;         /* I_max, default 100000 */
+    int64_t max_rejects;          /* default 85000 (0.85 I_max) */
+    double  hmin_factor;          /* h_min = hmin_factor * eps_m, default 100 */
+    double  wall_limit_s;         /* default 5400 (1.5 h) */
+    double  slow_limit_s;         /* default 2700 (45 min) ... */
+    double  slow_fraction;        /* ... with less than this fraction of [t0,t1] done, default 0.1 */
+    int64_t spin_limit;           /* polls of one grid barrier before BS3_ERR_DEVICE_WAIT, default 2^26 */
+} bs3_limits;
+
+/* Fills *lim with the paper's defaults (Sec. 2.2). */
+void bs3_default_limits(bs3_limits* lim);
+
+/* Name of a status code ("BS3_OK", ...); never NULL. */
+const char* bs3_status_string(int status);
+
+/* Creates a system of N agents of the given kind on CUDA device `device`.
+ * params: host array of n_params binary64 values, layout per bs3_kind above
+ * (copied; NULL allowed when n_params == 0).  stream: a cudaStream_t or NULL
+ * for the legacy default stream.  Allocates all per-system device buffers.
+ * Errors: BS3_ERR_INVALID_ARG (bad kind, N < 1, wrong n_params, out == NULL),
+ * BS3_ERR_CUDA (device selection or allocation failed). */
+int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_params,
+                      int device, void* stream, bs3_system_t* out);
+
+/* Stores the N x N coupling weights (Sec. 2.1: M_ij, with K, A or W folded in).
+ * K: row-major N*N values of type src (BS3_F64 or BS3_F32), host or device
+ * (is_device_ptr).  store: the element type kept on the device.  Quantisation
+ * rounds to binary32 first, then to `store` (nearest even), with per-row scales
+ * s_i: 1 for F64/F32/BF16; a power of two mapping each row's maximum into
+ * [2^14, 2^15) for F16; fp32(rowmax/448) for FP8E4M3 (saturating).  An all-zero
+ * row has s_i = 1.  Replaces any previous weights.  Must precede bs3_solve. */
+int bs3_set_coupling(bs3_system_t sys, const void* K, int src, int store, int is_device_ptr);
+
+/* Copies the stored weights back for inspection: q_out receives N*N values of
+ * the stored type (host memory, row-major, no padding), scales_out N binary32
+ * row scales (either may be NULL). */
+int bs3_get_coupling(bs3_system_t sys, void* q_out, float* scales_out);
+
+/* One right-hand-side evaluation out = f(t, y) (Eq. General-Model) with the
+ * precision triple (f_prec, sigma_prec, g_prec), each 0 = S, 1 = D, and the
+ * Sigma = D summation mode `accum`.  y, out: device pointers of d*N binary64.
+ * With f_prec = sigma_prec = g_prec = S the input is first rounded to binary32
+ * (the Single state) and the result holds binary32 values. */
+int bs3_rhs(bs3_system_t sys, double t, const double* y, int f_prec, int sigma_prec,
+            int g_prec, int accum, double* out);
+
+/* One BS3 attempt of size h from (t, X, K1) (Eq. Stage-ODE23, Eq. ERROR-O23):
+ * writes X^{n+1} to xn_out, K4 = f(t+h, X^{n+1}) to k4_out (device, d*N binary64)
+ * and the error E to *err_out (host).  No controller, no counters. */
+int bs3_attempt(bs3_system_t sys, double t, double h, const double* x, const double* k1,
+                double rtol, double atol, int variant, int accum,
+                double* xn_out, double* k4_out, double* err_out);
+
+/* Adaptive solve of the system from t0 to t1 > t0 (Sec. 2.2-2.3), entirely on
+ * the device in one persistent cooperative launch (no host round trip per step).
+ * y0: d*N binary64 initial state.  rtol > 0, atol >= 0 (Rel, Ab of Eq. ERROR-O23).
+ * variant: bs3_variant; accum: bs3_accum for Sigma = D stages.
+ * t_out: n_out requested output times, ascending, within [t0, t1]; y_out receives
+ * n_out * d*N values (dense output by cubic Hermite on each accepted step).
+ * flags: BS3_HOST_IO if y0/t_out/y_out are host pointers, else device pointers.
+ * final_y (optional, may be NULL): d*N state at t_reached, same memory kind as y_out.
+ * stats (host, optional), lim (host, NULL = bs3_default_limits).
+ * Returns the solve status (also in stats->status).  On a failure status the
+ * outputs with t_out <= t_reached and final_y are still written. */
+int bs3_solve(bs3_system_t sys, double t0, double t1, const double* y0, double rtol,
+              double atol, int variant, int accum, const double* t_out, int64_t n_out,
+              double* y_out, double* final_y, int flags, bs3_stats* stats,
+              const bs3_limits* lim);
+
+/* Frees the system and everything it owns.  NULL is allowed. */
+int bs3_destroy_system(bs3_system_t sys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BS3_H */

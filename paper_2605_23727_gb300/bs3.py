@@ -1,0 +1,233 @@
+"""ctypes binding of the C ABI in include/bs3.h (argument marshalling only).
+
+Every function keeps the C name.  Pointers are passed as Python ints (device
+addresses, e.g. ``tensor.data_ptr()``) or as numpy arrays (host memory).  The
+binding never computes any part of the method: a missing library raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbs3.so")
+
+# enums of bs3.h
+LCO_CFG, LCO_PAPER, KURAMOTO, CIRCADIAN = 0, 1, 2, 3
+SINGLE, MIXED1, MIXED2, DOUBLE = 0, 1, 2, 3
+F64, F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3, 4
+ACC_F32, ACC_FLOAT2, ACC_F64 = 0, 1, 2
+HOST_IO = 1
+OK = 0
+ERR_INVALID_ARG, ERR_CUDA, ERR_MAX_STEPS, ERR_MAX_REJECTS = 1, 2, 3, 4
+ERR_STEP_TOO_SMALL, ERR_TIMEOUT, ERR_DEVICE_WAIT, ERR_NONFINITE = 5, 6, 7, 8
+
+KIND_IDS = {"lco_cfg": LCO_CFG, "lco_paper": LCO_PAPER, "kuramoto": KURAMOTO, "circadian": CIRCADIAN}
+VARIANT_IDS = {"single": SINGLE, "mixed1": MIXED1, "mixed2": MIXED2, "double": DOUBLE}
+DTYPE_IDS = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16, "fp8e4m3": FP8E4M3}
+ACCUM_IDS = {"f32": ACC_F32, "float2": ACC_FLOAT2, "f64": ACC_F64}
+STORE_NUMPY = {F64: np.float64, F32: np.float32, BF16: np.uint16, F16: np.float16, FP8E4M3: np.uint8}
+
+EXPORTED = (
+    "bs3_default_limits", "bs3_status_string", "bs3_create_system", "bs3_set_coupling",
+    "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
+)
+
+
+class bs3_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_accepted", ctypes.c_int64),
+        ("n_rejected", ctypes.c_int64),
+        ("n_rhs_evals", ctypes.c_int64),
+        ("t_reached", ctypes.c_double),
+        ("h_last", ctypes.c_double),
+        ("status", ctypes.c_int32),
+        ("n_out_written", ctypes.c_int32),
+    ]
+
+
+class bs3_limits(ctypes.Structure):
+    _fields_ = [
+        ("max_attempts", ctypes.c_int64),
+        ("max_rejects", ctypes.c_int64),
+        ("hmin_factor", ctypes.c_double),
+        ("wall_limit_s", ctypes.c_double),
+        ("slow_limit_s", ctypes.c_double),
+        ("slow_fraction", ctypes.c_double),
+        ("spin_limit", ctypes.c_int64),
+    ]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libbs3.so (raising if it was not built) and declares signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(path)
+    P, D, I, I64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "bs3_default_limits": (None, [ctypes.POINTER(bs3_limits)]),
+        "bs3_status_string": (ctypes.c_char_p, [I]),
+        "bs3_create_system": (I, [I, I64, P, I64, I, P, ctypes.POINTER(P)]),
+        "bs3_set_coupling": (I, [P, P, I, I, I]),
+        "bs3_get_coupling": (I, [P, P, P]),
+        "bs3_rhs": (I, [P, D, P, I, I, I, I, P]),
+        "bs3_attempt": (I, [P, D, D, P, P, D, D, I, I, P, P, ctypes.POINTER(D)]),
+        "bs3_solve": (I, [P, D, D, P, D, D, I, I, P, I64, P, P, I, ctypes.POINTER(bs3_stats),
+                          ctypes.POINTER(bs3_limits)]),
+        "bs3_destroy_system": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+# ---------------------------------------------------------------- C names
+def bs3_default_limits() -> bs3_limits:
+    lim = bs3_limits()
+    load().bs3_default_limits(ctypes.byref(lim))
+    return lim
+
+
+def bs3_status_string(status: int) -> str:
+    return load().bs3_status_string(status).decode()
+
+
+def bs3_create_system(kind: int, N: int, params, device: int = 0, stream: int = 0) -> int:
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    out = ctypes.c_void_p()
+    rc = load().bs3_create_system(kind, N, _ptr(p), 0 if p is None else p.size, device, stream or None,
+                                  ctypes.byref(out))
+    if rc != OK:
+        raise RuntimeError(f"bs3_create_system: {bs3_status_string(rc)}")
+    return out.value
+
+
+def bs3_set_coupling(sys_: int, K, src: int, store: int, is_device_ptr: bool) -> int:
+    return load().bs3_set_coupling(sys_, _ptr(K), src, store, int(is_device_ptr))
+
+
+def bs3_get_coupling(sys_: int, q_out, scales_out) -> int:
+    return load().bs3_get_coupling(sys_, _ptr(q_out), _ptr(scales_out))
+
+
+def bs3_rhs(sys_: int, t: float, y, f_prec: int, sigma_prec: int, g_prec: int, accum: int, out) -> int:
+    return load().bs3_rhs(sys_, t, _ptr(y), f_prec, sigma_prec, g_prec, accum, _ptr(out))
+
+
+def bs3_attempt(sys_: int, t: float, h: float, x, k1, rtol: float, atol: float, variant: int, accum: int,
+                xn_out, k4_out):
+    err = ctypes.c_double()
+    rc = load().bs3_attempt(sys_, t, h, _ptr(x), _ptr(k1), rtol, atol, variant, accum, _ptr(xn_out),
+                            _ptr(k4_out), ctypes.byref(err))
+    return rc, err.value
+
+
+def bs3_solve(sys_: int, t0: float, t1: float, y0, rtol: float, atol: float, variant: int, accum: int,
+              t_out, n_out: int, y_out, final_y, flags: int, limits: Optional[bs3_limits] = None):
+    st = bs3_stats()
+    rc = load().bs3_solve(sys_, t0, t1, _ptr(y0), rtol, atol, variant, accum, _ptr(t_out), n_out,
+                          _ptr(y_out), _ptr(final_y), flags, ctypes.byref(st),
+                          None if limits is None else ctypes.byref(limits))
+    return rc, st
+
+
+def bs3_destroy_system(sys_: int) -> int:
+    return load().bs3_destroy_system(sys_)
+
+
+# ------------------------------------------------------------ convenience
+class System:
+    """Owns one bs3 system; host numpy in, host numpy out (BS3_HOST_IO)."""
+
+    def __init__(self, kind: str, N: int, params=None, globals_=None, device: int = 0, stream: int = 0):
+        self.kind = kind
+        self.N = N
+        self.d = {"lco_cfg": 2, "lco_paper": 2, "kuramoto": 1, "circadian": 4}[kind]
+        p = params
+        if kind == "circadian":
+            g = globals_
+            p = np.concatenate([np.asarray(params, dtype=np.float64),
+                                [g["k0"], g["k2"], g["k3"], g["a"], g["b"], g["c"], g["eps"], g["I0"]]])
+        if kind == "lco_paper":
+            p = None
+        self.handle = bs3_create_system(KIND_IDS[kind], N, p, device, stream)
+
+    @classmethod
+    def from_workload(cls, w, store: str = "f64", device: int = 0, stream: int = 0) -> "System":
+        s = cls(w.kind, w.N, w.params, w.globals, device, stream)
+        s.set_coupling(w.coupling, store)
+        return s
+
+    def set_coupling(self, K, store: str) -> None:
+        if hasattr(K, "data_ptr"):
+            src = F64 if str(K.dtype) == "torch.float64" else F32
+            rc = bs3_set_coupling(self.handle, K.data_ptr(), src, DTYPE_IDS[store], True)
+        else:
+            K = np.ascontiguousarray(K)
+            if K.dtype not in (np.float64, np.float32):
+                K = K.astype(np.float64)
+            src = F64 if K.dtype == np.float64 else F32
+            rc = bs3_set_coupling(self.handle, K, src, DTYPE_IDS[store], False)
+        if rc != OK:
+            raise RuntimeError(f"bs3_set_coupling: {bs3_status_string(rc)}")
+        self.store = store
+
+    def get_coupling(self):
+        st = DTYPE_IDS[self.store]
+        q = np.empty((self.N, self.N), dtype=STORE_NUMPY[st])
+        s = np.empty(self.N, dtype=np.float32)
+        rc = bs3_get_coupling(self.handle, q, s)
+        if rc != OK:
+            raise RuntimeError(bs3_status_string(rc))
+        return q, s
+
+    def solve(self, t0, t1, y0, rtol, atol, variant="double", accum="float2", t_out=None,
+              limits: Optional[bs3_limits] = None):
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        t_out = np.ascontiguousarray([] if t_out is None else t_out, dtype=np.float64)
+        n = self.d * self.N
+        y_out = np.zeros((len(t_out), n))
+        final = np.zeros(n)
+        rc, st = bs3_solve(self.handle, t0, t1, y0, rtol, atol, VARIANT_IDS[variant], ACCUM_IDS[accum],
+                           t_out if len(t_out) else None, len(t_out), y_out if len(t_out) else None,
+                           final, HOST_IO, limits)
+        return rc, st, final, y_out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            bs3_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,608 @@
+// Host side of the C ABI declared in include/bs3.h: system lifecycle,
+// quantisation of the coupling weights, launches of the persistent solver
+// and the wall-clock watchdog of Sec. 2.2.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "../../include/bs3.h"
+#include "bs3_device.cuh"
+#include "bs3_kernels.h"
+#include "bs3_solver.cuh"
+
+using namespace bs3;
+
+struct bs3_system {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int kind = 0, d = 1;
+  int64_t N = 0, ld = 0;
+  int store = -1;
+  // per-agent parameters
+  double* par = nullptr;
+  double* theta_h = nullptr;
+  double* rowsum = nullptr;
+  double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // stored weights
+  void* q = nullptr;
+  float* scale = nullptr;
+  // state and stage buffers
+  double* X = nullptr;
+  double* Xn = nullptr;
+  double* Kb[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* jv32 = nullptr;
+  double* jv64 = nullptr;
+  Control* ctrl = nullptr;
+  // host-mapped watchdog words
+  int* cancel_h = nullptr;
+  int* cancel_d = nullptr;
+  double* progress_h = nullptr;
+  double* progress_d = nullptr;
+  // staging for host input/output
+  double* stage_in = nullptr;
+  size_t stage_in_n = 0;
+  double* stage_out = nullptr;
+  size_t stage_out_n = 0;
+  int grid = 0;
+  int grid_store = -1;
+};
+
+namespace {
+
+size_t store_bytes(int st) {
+  switch (st) {
+    case ST_F64: return 8;
+    case ST_F32: return 4;
+    case ST_BF16:
+    case ST_F16: return 2;
+    default: return 1;
+  }
+}
+
+#define BS3_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return BS3_ERR_CUDA; \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+const void* kernel_for(int kind, int st) {
+  switch (kind) {
+    case BS3_LCO_CFG: return kernel_lco_cfg(st);
+    case BS3_LCO_PAPER: return kernel_lco_paper(st);
+    case BS3_KURAMOTO: return kernel_kuramoto(st);
+    default: return kernel_circadian(st);
+  }
+}
+
+// ---------------------------------------------------------------- quantise
+// Row maxima of |fp32(K_ij)| (one CTA per row).
+template <typename Src>
+__global__ void row_amax_kernel(const Src* __restrict__ K, int64_t N, float* __restrict__ amax) {
+  const int64_t i = blockIdx.x;
+  float m = 0.f;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) m = fmaxf(m, fabsf((float)K[i * N + j]));
+  __shared__ float sm[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sm[w]);
+    amax[i] = r;
+  }
+}
+
+__global__ void scale_kernel(const float* __restrict__ amax, int64_t N, int st, float* __restrict__ s) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float m = amax[i];
+  float r = 1.f;
+  if (m > 0.f && isfinite(m)) {
+    if (st == ST_F16) {
+      int k;
+      frexpf(m, &k);                       // m = f 2^k, f in [0.5, 1)
+      r = ldexpf(1.f, max(k - 1 - 14, -126));
+    } else if (st == ST_FP8) {
+      r = __fdiv_rn(m, 448.0f);
+    }
+  }
+  s[i] = r;
+}
+
+// q_ij = round_store(fp32(K_ij) / s_i) into the padded [N][ld] layout.
+template <typename Src>
+__global__ void quantize_kernel(const Src* __restrict__ K, int64_t N, int64_t ld, int st, int src_is_f64,
+                                const float* __restrict__ s, void* __restrict__ q) {
+  const int64_t total = N * ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ld, j = e - i * ld;
+    const bool in = j < N;
+    switch (st) {
+      case ST_F64: {
+        double v = 0.0;
+        if (in) v = src_is_f64 ? (double)K[i * N + j] : (double)(float)K[i * N + j];
+        ((double*)q)[e] = v;
+        break;
+      }
+      case ST_F32:
+        ((float*)q)[e] = in ? (float)K[i * N + j] : 0.f;
+        break;
+      case ST_BF16:
+        ((__nv_bfloat16*)q)[e] = __float2bfloat16_rn(in ? (float)K[i * N + j] : 0.f);
+        break;
+      case ST_F16:
+        ((__half*)q)[e] = __float2half_rn(in ? __fdiv_rn((float)K[i * N + j], s[i]) : 0.f);
+        break;
+      default:
+        ((__nv_fp8_storage_t*)q)[e] =
+            __nv_cvt_float_to_fp8(in ? __fdiv_rn((float)K[i * N + j], s[i]) : 0.f, __NV_SATFINITE, __NV_E4M3);
+        break;
+    }
+  }
+}
+
+// rowsum_i = s_i * sum_j q_ij in binary64 (paper-form oscillators).
+__global__ void rowsum_kernel(const void* __restrict__ q, int st, int64_t N, int64_t ld,
+                              const float* __restrict__ s, double* __restrict__ out) {
+  const int64_t i = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+    double v;
+    const int64_t e = i * ld + j;
+    switch (st) {
+      case ST_F64: v = ((const double*)q)[e]; break;
+      case ST_F32: v = ((const float*)q)[e]; break;
+      case ST_BF16: v = __bfloat162float(((const __nv_bfloat16*)q)[e]); break;
+      case ST_F16: v = __half2float(((const __half*)q)[e]); break;
+      default: {
+        const __half_raw hr = __nv_cvt_fp8_to_halfraw(((const __nv_fp8_storage_t*)q)[e], __NV_E4M3);
+        v = __half2float(__half(hr));
+      }
+    }
+    acc += v;
+  }
+  __shared__ double sm[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sm[w];
+    out[i] = (double)s[i] * r;
+  }
+}
+
+int ensure_stage(double** buf, size_t* cap, size_t n) {
+  if (*cap >= n && *buf) return BS3_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  BS3_CUDA(cudaMalloc(buf, std::max<size_t>(n, 1) * sizeof(double)));
+  *cap = n;
+  return BS3_OK;
+}
+
+int pick_grid(bs3_system* s) {
+  if (s->grid_store == s->store && s->grid > 0) return BS3_OK;
+  const void* k = kernel_for(s->kind, s->store);
+  int nb = 0, sms = 0;
+  BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, 0));
+  BS3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+  if (nb < 1) return BS3_ERR_CUDA;
+  const int rb = rows_per_tile(s->kind);
+  const int64_t ntiles = (s->N + rb - 1) / rb;
+  int64_t grid = (int64_t)nb * sms;
+  grid = std::min<int64_t>(grid, std::max<int64_t>(1, ntiles));
+  s->grid = (int)grid;
+  s->grid_store = s->store;
+  return BS3_OK;
+}
+
+void fill_args(const bs3_system* s, Args& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.N = (int)s->N;
+  a.ld = (int)s->ld;
+  a.q = s->q;
+  a.scale = s->scale;
+  a.rowsum = s->rowsum;
+  a.par = s->par;
+  a.theta_h = s->theta_h;
+  for (int k = 0; k < 8; ++k) a.g[k] = s->g[k];
+  a.X = s->X;
+  a.Xn = s->Xn;
+  for (int k = 0; k < 4; ++k) a.Kb[k] = s->Kb[k];
+  a.jv32 = s->jv32;
+  a.jv64 = s->jv64;
+  a.ctrl = s->ctrl;
+  a.cancel = s->cancel_d;
+  a.progress = s->progress_d;
+  a.spin_limit = (long long)1 << 26;
+  a.max_attempts = 100000;
+  a.max_rejects = 85000;
+  a.rtol = 1.0;
+  a.atol = 1.0;
+}
+
+int launch(bs3_system* s, Args& a) {
+  int rc = pick_grid(s);
+  if (rc != BS3_OK) return rc;
+  BS3_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(Control), s->stream));
+  void* params[] = {&a};
+  BS3_CUDA(cudaLaunchCooperativeKernel(kernel_for(s->kind, s->store), dim3(s->grid), dim3(kBlock), params, 0,
+                                       s->stream));
+  return BS3_OK;
+}
+
+// Waits for the stream, enforcing the wall-clock failure conditions through
+// the host-mapped cancel flag that the device polls once per attempt.
+int wait_with_watchdog(bs3_system* s, const bs3_limits& lim, double t0, double t1) {
+  const auto start = std::chrono::steady_clock::now();
+  int spins = 0;
+  while (true) {
+    const cudaError_t q = cudaStreamQuery(s->stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return BS3_ERR_CUDA;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - start).count();
+    const double done = (*(volatile double*)s->progress_h - t0) / (t1 - t0);
+    if (el > lim.wall_limit_s || (el > lim.slow_limit_s && done < lim.slow_fraction))
+      *(volatile int*)s->cancel_h = 1;
+    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  return BS3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bs3_default_limits(bs3_limits* lim) {
+  if (!lim) return;
+  lim->max_attempts = 100000;
+  lim->max_rejects = 85000;
+  lim->hmin_factor = 100.0;
+  lim->wall_limit_s = 1.5 * 3600.0;
+  lim->slow_limit_s = 45.0 * 60.0;
+  lim->slow_fraction = 0.1;
+  lim->spin_limit = (int64_t)1 << 26;
+}
+
+const char* bs3_status_string(int status) {
+  switch (status) {
+    case BS3_OK: return "BS3_OK";
+    case BS3_ERR_INVALID_ARG: return "BS3_ERR_INVALID_ARG";
+    case BS3_ERR_CUDA: return "BS3_ERR_CUDA";
+    case BS3_ERR_MAX_STEPS: return "BS3_ERR_MAX_STEPS";
+    case BS3_ERR_MAX_REJECTS: return "BS3_ERR_MAX_REJECTS";
+    case BS3_ERR_STEP_TOO_SMALL: return "BS3_ERR_STEP_TOO_SMALL";
+    case BS3_ERR_TIMEOUT: return "BS3_ERR_TIMEOUT";
+    case BS3_ERR_DEVICE_WAIT: return "BS3_ERR_DEVICE_WAIT";
+    case BS3_ERR_NONFINITE: return "BS3_ERR_NONFINITE";
+    default: return "BS3_UNKNOWN_STATUS";
+  }
+}
+
+int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_params, int device, void* stream,
+                      bs3_system_t* out) {
+  if (!out) return BS3_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (kind < BS3_LCO_CFG || kind > BS3_CIRCADIAN || N < 1 || N > (int64_t)1 << 30) return BS3_ERR_INVALID_ARG;
+  const int64_t need = (kind == BS3_LCO_PAPER) ? 0 : (kind == BS3_CIRCADIAN ? N + 8 : N);
+  if (n_params != need || (need > 0 && !params)) return BS3_ERR_INVALID_ARG;
+  if (kind == BS3_CIRCADIAN) {
+    const double k0 = params[N];
+    for (int64_t i = 0; i < N; ++i)
+      if (!(params[i] < k0) || !(params[i] > 0.0)) return BS3_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BS3_ERR_CUDA;
+  DeviceGuard guard(device);
+  bs3_system* s = new bs3_system();
+  s->device = device;
+  s->stream = (cudaStream_t)stream;
+  s->kind = kind;
+  s->d = (kind == BS3_KURAMOTO) ? 1 : (kind == BS3_CIRCADIAN ? 4 : 2);
+  s->N = N;
+  s->ld = (N + 15) / 16 * 16;
+  const size_t dN = (size_t)s->d * N;
+  auto fail = [&](int rc) {
+    bs3_destroy_system(s);
+    return rc;
+  };
+  if (cudaMalloc(&s->par, N * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMemset(s->par, 0, N * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (kind == BS3_LCO_CFG || kind == BS3_KURAMOTO || kind == BS3_CIRCADIAN) {
+    if (cudaMemcpy(s->par, params, N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(BS3_ERR_CUDA);
+  }
+  if (kind == BS3_CIRCADIAN) {
+    for (int k = 0; k < 8; ++k) s->g[k] = params[N + k];
+    std::vector<double> th(N);
+    for (int64_t i = 0; i < N; ++i) th[i] = params[i] / (s->g[0] - params[i]);
+    if (cudaMalloc(&s->theta_h, N * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+    if (cudaMemcpy(s->theta_h, th.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(BS3_ERR_CUDA);
+  }
+  if (cudaMalloc(&s->rowsum, N * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->scale, N * sizeof(float)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->X, dN * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->Xn, dN * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  for (int k = 0; k < 4; ++k)
+    if (cudaMalloc(&s->Kb[k], dN * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->jv32, 6 * s->ld * sizeof(float)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->jv64, 6 * s->ld * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMemset(s->jv32, 0, 6 * s->ld * sizeof(float)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMemset(s->jv64, 0, 6 * s->ld * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->ctrl, sizeof(Control)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaHostAlloc(&s->cancel_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaHostAlloc(&s->progress_h, sizeof(double), cudaHostAllocMapped) != cudaSuccess)
+    return fail(BS3_ERR_CUDA);
+  if (cudaHostGetDevicePointer((void**)&s->cancel_d, s->cancel_h, 0) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaHostGetDevicePointer((void**)&s->progress_d, s->progress_h, 0) != cudaSuccess)
+    return fail(BS3_ERR_CUDA);
+  *s->cancel_h = 0;
+  *s->progress_h = 0.0;
+  *out = s;
+  return BS3_OK;
+}
+
+int bs3_destroy_system(bs3_system_t s) {
+  if (!s) return BS3_OK;
+  DeviceGuard guard(s->device);
+  cudaFree(s->par);
+  cudaFree(s->theta_h);
+  cudaFree(s->rowsum);
+  cudaFree(s->q);
+  cudaFree(s->scale);
+  cudaFree(s->X);
+  cudaFree(s->Xn);
+  for (int k = 0; k < 4; ++k) cudaFree(s->Kb[k]);
+  cudaFree(s->jv32);
+  cudaFree(s->jv64);
+  cudaFree(s->ctrl);
+  cudaFree(s->stage_in);
+  cudaFree(s->stage_out);
+  if (s->cancel_h) cudaFreeHost(s->cancel_h);
+  if (s->progress_h) cudaFreeHost(s->progress_h);
+  delete s;
+  return BS3_OK;
+}
+
+int bs3_set_coupling(bs3_system_t s, const void* K, int src, int store, int is_device_ptr) {
+  if (!s || !K) return BS3_ERR_INVALID_ARG;
+  if ((src != BS3_F64 && src != BS3_F32) || store < BS3_F64 || store > BS3_FP8E4M3) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  const int64_t N = s->N, ld = s->ld;
+  const size_t sb = (src == BS3_F64) ? 8 : 4;
+  const size_t nbytes = (size_t)N * N * sb;
+  const void* dK = K;
+  void* tmp = nullptr;
+  if (!is_device_ptr) {
+    BS3_CUDA(cudaMalloc(&tmp, nbytes));
+    if (cudaMemcpyAsync(tmp, K, nbytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+      cudaFree(tmp);
+      return BS3_ERR_CUDA;
+    }
+    dK = tmp;
+  }
+  if (s->q) {
+    cudaFree(s->q);
+    s->q = nullptr;
+  }
+  int rc = BS3_OK;
+  float* amax = nullptr;
+  do {
+    if (cudaMalloc(&s->q, (size_t)N * ld * store_bytes(store)) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    if (cudaMalloc(&amax, N * sizeof(float)) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    const int blocks = (int)std::min<int64_t>((N * ld + 255) / 256, 152 * 64);
+    if (src == BS3_F64) {
+      row_amax_kernel<double><<<(unsigned)N, 256, 0, s->stream>>>((const double*)dK, N, amax);
+      scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s->stream>>>(amax, N, store, s->scale);
+      quantize_kernel<double><<<blocks, 256, 0, s->stream>>>((const double*)dK, N, ld, store, 1, s->scale, s->q);
+    } else {
+      row_amax_kernel<float><<<(unsigned)N, 256, 0, s->stream>>>((const float*)dK, N, amax);
+      scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s->stream>>>(amax, N, store, s->scale);
+      quantize_kernel<float><<<blocks, 256, 0, s->stream>>>((const float*)dK, N, ld, store, 0, s->scale, s->q);
+    }
+    rowsum_kernel<<<(unsigned)N, 256, 0, s->stream>>>(s->q, store, N, ld, s->scale, s->rowsum);
+    if (cudaGetLastError() != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+  } while (0);
+  if (amax) cudaFree(amax);
+  if (tmp) cudaFree(tmp);
+  if (rc != BS3_OK) {
+    if (s->q) cudaFree(s->q);
+    s->q = nullptr;
+    s->store = -1;
+    return rc;
+  }
+  s->store = store;
+  return BS3_OK;
+}
+
+int bs3_get_coupling(bs3_system_t s, void* q_out, float* scales_out) {
+  if (!s || s->store < 0) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  const size_t eb = store_bytes(s->store);
+  if (q_out)
+    BS3_CUDA(cudaMemcpy2DAsync(q_out, s->N * eb, s->q, s->ld * eb, s->N * eb, s->N, cudaMemcpyDeviceToHost,
+                               s->stream));
+  if (scales_out)
+    BS3_CUDA(cudaMemcpyAsync(scales_out, s->scale, s->N * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  BS3_CUDA(cudaStreamSynchronize(s->stream));
+  return BS3_OK;
+}
+
+int bs3_rhs(bs3_system_t s, double t, const double* y, int f_prec, int sigma_prec, int g_prec, int accum,
+            double* out) {
+  (void)t;  // the benchmark systems are autonomous
+  if (!s || !y || !out || s->store < 0) return BS3_ERR_INVALID_ARG;
+  if ((f_prec | sigma_prec | g_prec) & ~1 || accum < BS3_ACC_F32 || accum > BS3_ACC_F64) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  const size_t dN = (size_t)s->d * s->N;
+  BS3_CUDA(cudaMemcpyAsync(s->X, y, dN * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  Args a;
+  fill_args(s, a);
+  a.job = JOB_RHS;
+  a.accum = accum;
+  a.rhs_f = f_prec;
+  a.rhs_s = sigma_prec;
+  a.rhs_g = g_prec;
+  a.out0 = out;
+  int rc = launch(s, a);
+  if (rc != BS3_OK) return rc;
+  BS3_CUDA(cudaStreamSynchronize(s->stream));
+  int st = 0;
+  BS3_CUDA(cudaMemcpy(&st, &s->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost));
+  return st == 0 ? BS3_OK : st;
+}
+
+int bs3_attempt(bs3_system_t s, double t, double h, const double* x, const double* k1, double rtol, double atol,
+                int variant, int accum, double* xn_out, double* k4_out, double* err_out) {
+  if (!s || !x || !k1 || !xn_out || !k4_out || !err_out || s->store < 0) return BS3_ERR_INVALID_ARG;
+  if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64)
+    return BS3_ERR_INVALID_ARG;
+  if (!(h > 0.0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  const size_t dN = (size_t)s->d * s->N;
+  BS3_CUDA(cudaMemcpyAsync(s->X, x, dN * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  BS3_CUDA(cudaMemcpyAsync(s->Kb[0], k1, dN * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  Args a;
+  fill_args(s, a);
+  a.job = JOB_ATTEMPT;
+  a.variant = variant;
+  a.accum = accum;
+  a.t0 = t;
+  a.t1 = t + h;
+  a.h_given = h;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.out0 = xn_out;
+  a.out1 = k4_out;
+  int rc = launch(s, a);
+  if (rc != BS3_OK) return rc;
+  BS3_CUDA(cudaStreamSynchronize(s->stream));
+  Control c;
+  BS3_CUDA(cudaMemcpy(&c, s->ctrl, sizeof(Control), cudaMemcpyDeviceToHost));
+  uint64_t bits = c.emax[0];
+  std::memcpy(err_out, &bits, sizeof(double));
+  return c.status == 0 ? BS3_OK : c.status;
+}
+
+int bs3_solve(bs3_system_t s, double t0, double t1, const double* y0, double rtol, double atol, int variant,
+              int accum, const double* t_out, int64_t n_out, double* y_out, double* final_y, int flags,
+              bs3_stats* stats, const bs3_limits* lim_in) {
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->status = BS3_ERR_INVALID_ARG;
+  }
+  if (!s || !y0 || s->store < 0) return BS3_ERR_INVALID_ARG;
+  if (!(t1 > t0) || !std::isfinite(t0) || !std::isfinite(t1)) return BS3_ERR_INVALID_ARG;
+  if (!(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
+  if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64)
+    return BS3_ERR_INVALID_ARG;
+  if (n_out < 0 || (n_out > 0 && (!t_out || !y_out))) return BS3_ERR_INVALID_ARG;
+  const bool host_io = (flags & BS3_HOST_IO) != 0;
+  if (host_io && n_out > 0) {
+    for (int64_t k = 0; k < n_out; ++k) {
+      if (!(t_out[k] >= t0 && t_out[k] <= t1)) return BS3_ERR_INVALID_ARG;
+      if (k > 0 && t_out[k] < t_out[k - 1]) return BS3_ERR_INVALID_ARG;
+    }
+  }
+  bs3_limits lim;
+  if (lim_in) lim = *lim_in;
+  else bs3_default_limits(&lim);
+  if (lim.max_attempts < 0 || lim.max_rejects < 0 || lim.spin_limit < 1) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  const size_t dN = (size_t)s->d * s->N;
+  int rc;
+  // inputs
+  const double* d_tout = t_out;
+  double* d_yout = y_out;
+  double* d_final = final_y;
+  if (host_io) {
+    rc = ensure_stage(&s->stage_in, &s->stage_in_n, (size_t)std::max<int64_t>(n_out, 1));
+    if (rc) return rc;
+    rc = ensure_stage(&s->stage_out, &s->stage_out_n, (size_t)n_out * dN + dN);
+    if (rc) return rc;
+    BS3_CUDA(cudaMemcpyAsync(s->X, y0, dN * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (n_out > 0)
+      BS3_CUDA(cudaMemcpyAsync(s->stage_in, t_out, n_out * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    d_tout = s->stage_in;
+    d_yout = s->stage_out;
+    d_final = final_y ? s->stage_out + (size_t)n_out * dN : nullptr;
+  } else {
+    BS3_CUDA(cudaMemcpyAsync(s->X, y0, dN * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  }
+  *(volatile int*)s->cancel_h = 0;
+  *(volatile double*)s->progress_h = t0;
+  Args a;
+  fill_args(s, a);
+  a.job = JOB_SOLVE;
+  a.variant = variant;
+  a.accum = accum;
+  a.t0 = t0;
+  a.t1 = t1;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.hmin = lim.hmin_factor * (variant == BS3_SINGLE ? (double)FLT_EPSILON : DBL_EPSILON);
+  a.hmax = 0.1 * std::fabs(t1 - t0);
+  a.h_given = 0.0;
+  a.t_out = d_tout;
+  a.n_out = n_out;
+  a.y_out = d_yout;
+  a.final_y = d_final;
+  a.max_attempts = lim.max_attempts;
+  a.max_rejects = lim.max_rejects;
+  a.spin_limit = lim.spin_limit;
+  rc = launch(s, a);
+  if (rc != BS3_OK) return rc;
+  rc = wait_with_watchdog(s, lim, t0, t1);
+  if (rc != BS3_OK) return rc;
+  Control c;
+  BS3_CUDA(cudaMemcpy(&c, s->ctrl, sizeof(Control), cudaMemcpyDeviceToHost));
+  if (host_io) {
+    if (n_out > 0)
+      BS3_CUDA(cudaMemcpy(y_out, s->stage_out, (size_t)n_out * dN * sizeof(double), cudaMemcpyDeviceToHost));
+    if (final_y)
+      BS3_CUDA(cudaMemcpy(final_y, s->stage_out + (size_t)n_out * dN, dN * sizeof(double),
+                          cudaMemcpyDeviceToHost));
+  }
+  if (stats) {
+    stats->n_accepted = c.n_acc;
+    stats->n_rejected = c.n_rej;
+    stats->n_rhs_evals = c.n_rhs;
+    stats->t_reached = c.t;
+    stats->h_last = c.h;
+    stats->status = c.status;
+    stats->n_out_written = (int32_t)c.n_out;
+  }
+  return c.status;
+}
+
+}  // extern "C"

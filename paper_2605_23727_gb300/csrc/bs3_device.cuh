@@ -1,0 +1,234 @@
+// Device-side building blocks of the sm_103a BS3 solver: stored-weight
+// loaders, accumulators for the Sigma precisions of Table MP-Distrib
+// (Sec. 2.3), a bounded grid barrier and bit-pattern max reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace bs3 {
+
+enum Kind { K_LCO_CFG = 0, K_LCO_PAPER = 1, K_KURAMOTO = 2, K_CIRCADIAN = 3 };
+enum Store { ST_F64 = 0, ST_F32 = 1, ST_BF16 = 2, ST_F16 = 3, ST_FP8 = 4 };
+// Summation modes of one coupling evaluation:
+//   SS   G = S, Sigma = S: binary32 products, binary32 sum (fmaf)
+//   SD64 G = S, Sigma = D: binary32 products cast to binary64, binary64 sum
+//   SD2  G = S, Sigma = D: binary32 products, compensated float-float sum
+//   DD   G = D, Sigma = D: binary64 products and sum
+enum Mode { M_SS = 0, M_SD64 = 1, M_SD2 = 2, M_DD = 3 };
+enum Job { JOB_SOLVE = 0, JOB_RHS = 1, JOB_ATTEMPT = 2 };
+enum Variant { V_SINGLE = 0, V_MIXED1 = 1, V_MIXED2 = 2, V_DOUBLE = 3 };
+enum Accum { A_F32 = 0, A_FLOAT2 = 1, A_F64 = 2 };
+enum Status {
+  S_OK = 0, S_INVALID = 1, S_CUDA = 2, S_MAX_STEPS = 3, S_MAX_REJECTS = 4,
+  S_STEP_TOO_SMALL = 5, S_TIMEOUT = 6, S_DEVICE_WAIT = 7, S_NONFINITE = 8
+};
+
+constexpr int kBlock = 512;   // threads per CTA of the persistent solver
+constexpr int kRBMax = 4;     // largest number of rows per warp tile
+
+// Rows per warp tile: the streaming products share each j-vector chunk over 4
+// rows; the pairwise arctangent kernel is ALU-bound and keeps 2.
+__host__ __device__ constexpr int rows_per_tile(int kind) { return kind == K_CIRCADIAN ? 2 : 4; }
+
+// Persistent-solver control block (device memory, zeroed before each launch).
+struct Control {
+  unsigned long long bar;        // grid-barrier arrivals, monotonic
+  unsigned long long emax[2];    // bit patterns of E (non-negative binary64), by attempt parity
+  unsigned long long red[3];     // starting-step maxima d0, d1, d2
+  int status;                    // first failure wins (atomicCAS from 0)
+  int cancel_seen[2];            // host cancel flag latched by CTA 0, by attempt parity
+  int pad;
+  long long n_acc, n_rej, n_rhs, n_out;
+  double t, h;
+};
+
+// ---------------------------------------------------------------------------
+// Memory helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Streaming 16-byte load of weights that never change during a launch.
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
+// Grid barrier for a cooperative launch.  Every CTA adds one arrival to a
+// monotonic counter and waits until the counter reaches its target; the
+// wait is bounded by spin_limit polls, after which the status becomes
+// S_DEVICE_WAIT.  Returns false when the launch must stop (any failure).
+__device__ __forceinline__ bool grid_sync(Control* c, unsigned long long& target,
+                                          long long spin_limit, int* s_abort) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&c->bar, 1ULL);
+    long long it = 0;
+    while (ld_acquire_u64(&c->bar) < target) {
+      if (++it > spin_limit) {
+        atomicCAS(&c->status, 0, (int)S_DEVICE_WAIT);
+        break;
+      }
+      if (it > 32) __nanosleep(40);
+    }
+    *s_abort = (*(volatile int*)&c->status == (int)S_DEVICE_WAIT);
+  }
+  __syncthreads();
+  return !*s_abort;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
+  // non-negative binary64 (and NaN, whose bits compare above +Inf) order as u64
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Stored-weight loaders: one 16-byte chunk holds VEC elements.
+// ---------------------------------------------------------------------------
+template <int ST> struct KLoad;
+
+template <> struct KLoad<ST_F64> {
+  static constexpr int VEC = 2, BYTES = 8;
+  __device__ static __forceinline__ float f(const uint4& r, int e) {
+    return (float)get_d(r, e);
+  }
+  __device__ static __forceinline__ double get_d(const uint4& r, int e) {
+    return e == 0 ? __hiloint2double((int)r.y, (int)r.x) : __hiloint2double((int)r.w, (int)r.z);
+  }
+};
+template <> struct KLoad<ST_F32> {
+  static constexpr int VEC = 4, BYTES = 4;
+  __device__ static __forceinline__ float f(const uint4& r, int e) {
+    const uint32_t w = e == 0 ? r.x : e == 1 ? r.y : e == 2 ? r.z : r.w;
+    return __uint_as_float(w);
+  }
+  __device__ static __forceinline__ double get_d(const uint4& r, int e) { return (double)f(r, e); }
+};
+template <> struct KLoad<ST_BF16> {
+  static constexpr int VEC = 8, BYTES = 2;
+  __device__ static __forceinline__ float f(const uint4& r, int e) {
+    const uint32_t w = (e >> 1) == 0 ? r.x : (e >> 1) == 1 ? r.y : (e >> 1) == 2 ? r.z : r.w;
+    return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+  }
+  __device__ static __forceinline__ double get_d(const uint4& r, int e) { return (double)f(r, e); }
+};
+template <> struct KLoad<ST_F16> {
+  static constexpr int VEC = 8, BYTES = 2;
+  __device__ static __forceinline__ float f(const uint4& r, int e) {
+    const uint32_t w = (e >> 1) == 0 ? r.x : (e >> 1) == 1 ? r.y : (e >> 1) == 2 ? r.z : r.w;
+    const unsigned short hbits = (unsigned short)((e & 1) ? (w >> 16) : (w & 0xffffu));
+    return __half2float(__ushort_as_half(hbits));
+  }
+  __device__ static __forceinline__ double get_d(const uint4& r, int e) { return (double)f(r, e); }
+};
+template <> struct KLoad<ST_FP8> {
+  static constexpr int VEC = 16, BYTES = 1;
+  __device__ static __forceinline__ float f(const uint4& r, int e) {
+    const uint32_t w = (e >> 2) == 0 ? r.x : (e >> 2) == 1 ? r.y : (e >> 2) == 2 ? r.z : r.w;
+    const __nv_fp8_storage_t b = (__nv_fp8_storage_t)((w >> (8 * (e & 3))) & 0xffu);
+    const __half_raw h = __nv_cvt_fp8_to_halfraw(b, __NV_E4M3);
+    return __half2float(__half(h));
+  }
+  __device__ static __forceinline__ double get_d(const uint4& r, int e) { return (double)f(r, e); }
+};
+
+// ---------------------------------------------------------------------------
+// Accumulators
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int MODE> struct Acc;
+
+template <> struct Acc<M_SS> {
+  float s = 0.f;
+  __device__ __forceinline__ void add_f(float k, float v) { s = fmaf(k, v, s); }
+  __device__ __forceinline__ void add_d(double k, double v) { s = fmaf((float)k, (float)v, s); }
+  __device__ __forceinline__ void xor_merge(int off) { s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off)); }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <> struct Acc<M_SD64> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_f(float k, float v) { s = __dadd_rn(s, (double)__fmul_rn(k, v)); }
+  __device__ __forceinline__ void add_d(double k, double v) { add_f((float)k, (float)v); }
+  __device__ __forceinline__ void xor_merge(int off) { s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off)); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<M_SD2> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_f(float k, float v) {
+    float s, e;
+    two_sum(hi, __fmul_rn(k, v), s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_d(double k, double v) { add_f((float)k, (float)v); }
+  __device__ __forceinline__ void xor_merge(int off) {
+    const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+    const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+    float s, e;
+    two_sum(hi, ohi, s, e);
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, olo), e);
+  }
+  __device__ __forceinline__ double value() const { return __dadd_rn((double)hi, (double)lo); }
+};
+template <> struct Acc<M_DD> {
+  double s = 0.0;
+  __device__ __forceinline__ void add_f(float k, float v) { s = fma((double)k, (double)v, s); }
+  __device__ __forceinline__ void add_d(double k, double v) { s = fma(k, v, s); }
+  __device__ __forceinline__ void xor_merge(int off) { s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, off)); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// sin and cos of a binary64 phase, rounded to binary32: the phase is first
+// reduced to [-pi, pi] in binary64 (two-constant Cody-Waite with 2 pi split
+// into a 33-bit head and a binary64 tail), then evaluated in binary32.
+__device__ __forceinline__ void sincos_f_of_d(double th, float* s, float* c) {
+  const double kInv2Pi = 0.15915494309189535;
+  const double k2PiHi = 6.2831853069365025;             // 2 pi rounded to 33 bits
+  const double k2PiLo = 2.430840202602477e-10;           // 2 pi - k2PiHi
+  const double k = rint(th * kInv2Pi);
+  double r = fma(-k, k2PiHi, th);
+  r = fma(-k, k2PiLo, r);
+  sincosf((float)r, s, c);
+}
+
+// Arctangent in binary32 (the project's own): atan(x) = x P(x^2) on [0, 1]
+// with P the degree-8 minimax polynomial fitted by csrc/fit_atan.py (Lawson's
+// algorithm, relative error), and atan(x) = pi/2 - atan(1/x) above 1.  Max
+// error 1.8 ulp on the fit script's grid.
+__device__ __forceinline__ float atan_f32(float x) {
+  const float ax = fabsf(x);
+  const bool big = ax > 1.0f;
+  const float t = big ? __frcp_rn(ax) : ax;
+  const float z = t * t;
+  float p = 2.849889454e-03f;
+  p = fmaf(p, z, -1.606862806e-02f);
+  p = fmaf(p, z, 4.269151762e-02f);
+  p = fmaf(p, z, -7.504294813e-02f);
+  p = fmaf(p, z, 1.064093411e-01f);
+  p = fmaf(p, z, -1.420364380e-01f);
+  p = fmaf(p, z, 1.999261975e-01f);
+  p = fmaf(p, z, -3.333307207e-01f);
+  p = fmaf(p, z, 1.000000000e+00f);
+  float r = t * p;
+  r = big ? (1.57079637f - r) : r;
+  return copysignf(r, x);
+}
+
+}  // namespace bs3

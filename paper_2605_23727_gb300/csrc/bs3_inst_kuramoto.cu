@@ -1,0 +1,15 @@
+// Solver kernels for the Kuramoto kind (Eq. Kuramoto).
+#include "bs3_solver.cuh"
+#include "bs3_kernels.h"
+
+namespace bs3 {
+const void* kernel_kuramoto(int st) {
+  switch (st) {
+    case ST_F64: return (const void*)bs3_kernel<K_KURAMOTO, ST_F64>;
+    case ST_F32: return (const void*)bs3_kernel<K_KURAMOTO, ST_F32>;
+    case ST_BF16: return (const void*)bs3_kernel<K_KURAMOTO, ST_BF16>;
+    case ST_F16: return (const void*)bs3_kernel<K_KURAMOTO, ST_F16>;
+    default: return (const void*)bs3_kernel<K_KURAMOTO, ST_FP8>;
+  }
+}
+}  // namespace bs3
