@@ -166,6 +166,32 @@ int bs3_solve(bs3_system_t sys, double t0, double t1, const double* y0, double r
               double* y_out, double* final_y, int flags, bs3_stats* stats,
               const bs3_limits* lim);
 
+/* Tuning knobs (bs3_set_tuning keys). */
+enum {
+    /* 1 (default): when the weight rows of every CTA fit in its shared memory
+     * (one CTA per SM), load them once per solve and keep them on chip; 0:
+     * always stream them from HBM/L2 at every stage.  Results are identical. */
+    BS3_TUNE_RESIDENT_WEIGHTS = 1
+};
+
+/* Sets a tuning knob of the system (takes effect at the next launch).
+ * Errors: BS3_ERR_INVALID_ARG for an unknown key or value.  The paper has no
+ * counterpart (it concerns only how this library maps the method on the GPU). */
+int bs3_set_tuning(bs3_system_t sys, int key, int64_t value);
+
+/* Step history (tracing, and the training data of a learned step-size
+ * proposer): with capacity > 0, each later bs3_solve records its first
+ * `capacity` attempts, 8 binary64 values each: t, h, E (Eq. ERROR-O23),
+ * accepted (1/0), then the device time in ns from the start of the attempt
+ * to the end of each of its four grid barriers (as seen by CTA 0).
+ * capacity = 0 turns recording off and frees the buffer.  The paper has no
+ * counterpart (its metrics are computed offline from MATLAB runs). */
+int bs3_set_history(bs3_system_t sys, int64_t capacity);
+
+/* Copies the records of the last solve to out (host, at least capacity*8
+ * binary64) and their number to *n_records. */
+int bs3_get_history(bs3_system_t sys, double* out, int64_t* n_records);
+
 /* Frees the system and everything it owns.  NULL is allowed. */
 int bs3_destroy_system(bs3_system_t sys);
 

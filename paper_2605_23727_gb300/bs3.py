@@ -35,7 +35,9 @@ STORE_NUMPY = {F64: np.float64, F32: np.float32, BF16: np.uint16, F16: np.float1
 EXPORTED = (
     "bs3_default_limits", "bs3_status_string", "bs3_create_system", "bs3_set_coupling",
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
+    "bs3_set_history", "bs3_get_history", "bs3_set_tuning",
 )
+TUNE_RESIDENT_WEIGHTS = 1
 
 
 class bs3_stats(ctypes.Structure):
@@ -86,6 +88,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_solve": (I, [P, D, D, P, D, D, I, I, P, I64, P, P, I, ctypes.POINTER(bs3_stats),
                           ctypes.POINTER(bs3_limits)]),
         "bs3_destroy_system": (I, [P]),
+        "bs3_set_history": (I, [P, I64]),
+        "bs3_set_tuning": (I, [P, I, I64]),
+        "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -159,6 +164,22 @@ def bs3_solve(sys_: int, t0: float, t1: float, y0, rtol: float, atol: float, var
     return rc, st
 
 
+def bs3_set_tuning(sys_: int, key: int, value: int) -> int:
+    return load().bs3_set_tuning(sys_, key, value)
+
+
+def bs3_set_history(sys_: int, capacity: int) -> int:
+    return load().bs3_set_history(sys_, capacity)
+
+
+def bs3_get_history(sys_: int, capacity: int):
+    """Returns (rc, records[n, 8])."""
+    out = np.zeros((max(capacity, 1), 8))
+    n = ctypes.c_int64()
+    rc = load().bs3_get_history(sys_, _ptr(out), ctypes.byref(n))
+    return rc, out[:n.value]
+
+
 def bs3_destroy_system(sys_: int) -> int:
     return load().bs3_destroy_system(sys_)
 
@@ -181,9 +202,14 @@ class System:
         self.handle = bs3_create_system(KIND_IDS[kind], N, p, device, stream)
 
     @classmethod
-    def from_workload(cls, w, store: str = "f64", device: int = 0, stream: int = 0) -> "System":
+    def from_workload(cls, w, store: str = "f64", device: int = 0, stream: int = 0,
+                      resident: bool = True) -> "System":
         s = cls(w.kind, w.N, w.params, w.globals, device, stream)
         s.set_coupling(w.coupling, store)
+        if not resident:
+            rc = bs3_set_tuning(s.handle, TUNE_RESIDENT_WEIGHTS, 0)
+            if rc != OK:
+                raise RuntimeError(bs3_status_string(rc))
         return s
 
     def set_coupling(self, K, store: str) -> None:

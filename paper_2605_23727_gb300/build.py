@@ -18,12 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbs3.so")
 
-SOURCES = [
-    "bs3_api.cu",
-    "bs3_inst_lco.cu",
-    "bs3_inst_kuramoto.cu",
-    "bs3_inst_circadian.cu",
-]
+SOURCES = ["bs3_api.cu"] + sorted(f for f in os.listdir(CSRC) if f.startswith("inst_") and f.endswith(".cu"))
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
@@ -59,7 +54,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         newest = max(os.path.getmtime(p) for p in deps)
         if os.path.getmtime(LIB) >= newest:
             return LIB
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-Xcompiler", "-fPIC"]

@@ -53,7 +53,14 @@ struct bs3_system {
   size_t stage_in_n = 0;
   double* stage_out = nullptr;
   size_t stage_out_n = 0;
+  double* hist = nullptr;
+  int64_t hist_cap = 0;
+  int64_t hist_n = 0;
   int grid = 0;
+  int rc = 0;
+  size_t smem = 0;
+  int slab = 0;
+  bool allow_resident = true;
   int grid_store = -1;
 };
 
@@ -88,14 +95,7 @@ struct DeviceGuard {
   }
 };
 
-const void* kernel_for(int kind, int st) {
-  switch (kind) {
-    case BS3_LCO_CFG: return kernel_lco_cfg(st);
-    case BS3_LCO_PAPER: return kernel_lco_paper(st);
-    case BS3_KURAMOTO: return kernel_kuramoto(st);
-    default: return kernel_circadian(st);
-  }
-}
+const void* kernel_for(int kind, int st) { return kernel_lookup(kind, st); }
 
 // ---------------------------------------------------------------- quantise
 // Row maxima of |fp32(K_ij)| (one CTA per row).
@@ -208,18 +208,32 @@ int ensure_stage(double** buf, size_t* cap, size_t n) {
   return BS3_OK;
 }
 
+// One CTA per SM (at most one per row block of agents).  Each CTA keeps the
+// state of ceil(N / grid) agents in shared memory.
 int pick_grid(bs3_system* s) {
   if (s->grid_store == s->store && s->grid > 0) return BS3_OK;
   const void* k = kernel_for(s->kind, s->store);
-  int nb = 0, sms = 0;
-  BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, 0));
+  int sms = 0;
   BS3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-  if (nb < 1) return BS3_ERR_CUDA;
   const int rb = rows_per_tile(s->kind);
-  const int64_t ntiles = (s->N + rb - 1) / rb;
-  int64_t grid = (int64_t)nb * sms;
-  grid = std::min<int64_t>(grid, std::max<int64_t>(1, ntiles));
+  const int64_t grid = std::min<int64_t>(sms, std::max<int64_t>(1, (s->N + rb - 1) / rb));
+  const int rc = (int)((s->N + grid - 1) / grid);
+  const size_t state = state_smem_bytes(s->d, rc);
+  if (state > (size_t)200 * 1024) return BS3_ERR_INVALID_ARG;
+  // keep each CTA's weight rows resident in shared memory when they fit
+  // (streaming kinds only; the pairwise arctangent kernel is ALU-bound)
+  const size_t slab = ((size_t)rc * s->ld * store_bytes(s->store) + 127) / 128 * 128;
+  const size_t budget = (size_t)224 * 1024;
+  const bool resident = s->kind != BS3_CIRCADIAN && s->allow_resident && slab + state <= budget;
+  const size_t smem = (resident ? slab : 0) + state;
+  BS3_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int nb = 0;
+  BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem));
+  if (nb < 1) return BS3_ERR_CUDA;
   s->grid = (int)grid;
+  s->rc = rc;
+  s->smem = smem;
+  s->slab = resident ? (int)slab : 0;
   s->grid_store = s->store;
   return BS3_OK;
 }
@@ -252,10 +266,12 @@ void fill_args(const bs3_system* s, Args& a) {
 int launch(bs3_system* s, Args& a) {
   int rc = pick_grid(s);
   if (rc != BS3_OK) return rc;
+  a.rc = s->rc;
+  a.slab_bytes = s->slab;
   BS3_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(Control), s->stream));
   void* params[] = {&a};
-  BS3_CUDA(cudaLaunchCooperativeKernel(kernel_for(s->kind, s->store), dim3(s->grid), dim3(kBlock), params, 0,
-                                       s->stream));
+  BS3_CUDA(cudaLaunchCooperativeKernel(kernel_for(s->kind, s->store), dim3(s->grid), dim3(kBlock), params,
+                                       s->smem, s->stream));
   return BS3_OK;
 }
 
@@ -371,6 +387,41 @@ int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_param
   return BS3_OK;
 }
 
+int bs3_set_tuning(bs3_system_t s, int key, int64_t value) {
+  if (!s) return BS3_ERR_INVALID_ARG;
+  if (key == BS3_TUNE_RESIDENT_WEIGHTS) {
+    if (value != 0 && value != 1) return BS3_ERR_INVALID_ARG;
+    s->allow_resident = value != 0;
+    s->grid_store = -1;   // re-plan the launch
+    return BS3_OK;
+  }
+  return BS3_ERR_INVALID_ARG;
+}
+
+int bs3_set_history(bs3_system_t s, int64_t capacity) {
+  if (!s || capacity < 0) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  if (s->hist) cudaFree(s->hist);
+  s->hist = nullptr;
+  s->hist_cap = 0;
+  s->hist_n = 0;
+  if (capacity == 0) return BS3_OK;
+  BS3_CUDA(cudaMalloc(&s->hist, (size_t)capacity * kHistDoubles * sizeof(double)));
+  s->hist_cap = capacity;
+  return BS3_OK;
+}
+
+int bs3_get_history(bs3_system_t s, double* out, int64_t* n_records) {
+  if (!s || !n_records) return BS3_ERR_INVALID_ARG;
+  *n_records = s->hist_n;
+  if (s->hist_n > 0) {
+    if (!out) return BS3_ERR_INVALID_ARG;
+    DeviceGuard guard(s->device);
+    BS3_CUDA(cudaMemcpy(out, s->hist, (size_t)s->hist_n * kHistDoubles * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return BS3_OK;
+}
+
 int bs3_destroy_system(bs3_system_t s) {
   if (!s) return BS3_OK;
   DeviceGuard guard(s->device);
@@ -387,6 +438,7 @@ int bs3_destroy_system(bs3_system_t s) {
   cudaFree(s->ctrl);
   cudaFree(s->stage_in);
   cudaFree(s->stage_out);
+  cudaFree(s->hist);
   if (s->cancel_h) cudaFreeHost(s->cancel_h);
   if (s->progress_h) cudaFreeHost(s->progress_h);
   delete s;
@@ -580,6 +632,8 @@ int bs3_solve(bs3_system_t s, double t0, double t1, const double* y0, double rto
   a.max_attempts = lim.max_attempts;
   a.max_rejects = lim.max_rejects;
   a.spin_limit = lim.spin_limit;
+  a.hist = s->hist;
+  a.hist_cap = s->hist_cap;
   rc = launch(s, a);
   if (rc != BS3_OK) return rc;
   rc = wait_with_watchdog(s, lim, t0, t1);
@@ -593,6 +647,7 @@ int bs3_solve(bs3_system_t s, double t0, double t1, const double* y0, double rto
       BS3_CUDA(cudaMemcpy(final_y, s->stage_out + (size_t)n_out * dN, dN * sizeof(double),
                           cudaMemcpyDeviceToHost));
   }
+  s->hist_n = std::min<int64_t>(s->hist_cap, c.n_acc + c.n_rej);
   if (stats) {
     stats->n_accepted = c.n_acc;
     stats->n_rejected = c.n_rej;

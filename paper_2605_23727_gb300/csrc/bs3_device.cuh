@@ -27,10 +27,12 @@ enum Status {
   S_STEP_TOO_SMALL = 5, S_TIMEOUT = 6, S_DEVICE_WAIT = 7, S_NONFINITE = 8
 };
 
-constexpr int kBlock = 512;   // threads per CTA of the persistent solver
-constexpr int kRBMax = 4;     // largest number of rows per warp tile
+constexpr int kBlock = 512;          // threads per CTA of the persistent solver
+constexpr int kGroupThreads = 128;   // a warp group: four warps share one row block
+constexpr int kGroups = kBlock / kGroupThreads;
+constexpr int kRBMax = 4;            // largest number of rows per row block
 
-// Rows per warp tile: the streaming products share each j-vector chunk over 4
+// Rows per row block: the streaming products share each j-vector chunk over 4
 // rows; the pairwise arctangent kernel is ALU-bound and keeps 2.
 __host__ __device__ constexpr int rows_per_tile(int kind) { return kind == K_CIRCADIAN ? 2 : 4; }
 
@@ -45,6 +47,11 @@ struct Control {
   long long n_acc, n_rej, n_rhs, n_out;
   double t, h;
 };
+
+// One record per attempt of a solve (optional): t, h, E, accepted, then the
+// device time (ns, %globaltimer) spent by CTA 0 from the start of the attempt
+// to the end of each of its four barriers (A, B2, B3, B4).
+constexpr int kHistDoubles = 8;
 
 // ---------------------------------------------------------------------------
 // Memory helpers
@@ -64,25 +71,39 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
 }
 
 // Grid barrier for a cooperative launch.  Every CTA adds one arrival to a
-// monotonic counter and waits until the counter reaches its target; the
-// wait is bounded by spin_limit polls, after which the status becomes
-// S_DEVICE_WAIT.  Returns false when the launch must stop (any failure).
+// monotonic counter (release) and polls it until it reaches its target.  The
+// wait is bounded by spin_limit polls; a CTA that gives up sets the status to
+// S_DEVICE_WAIT and adds kAbortBias to the counter, which every other waiter
+// sees in the same poll.  Returns false when the launch must stop.
+constexpr unsigned long long kAbortBias = 1ull << 48;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_sync(Control* c, unsigned long long& target,
                                           long long spin_limit, int* s_abort) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(&c->bar, 1ULL);
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" :: "l"(&c->bar) : "memory");
     long long it = 0;
-    while (ld_acquire_u64(&c->bar) < target) {
+    int abort = 0;
+    while (true) {
+      const unsigned long long v = ld_acquire_u64(&c->bar);
+      if (v >= kAbortBias) { abort = 1; break; }
+      if (v >= target) break;
       if (++it > spin_limit) {
         atomicCAS(&c->status, 0, (int)S_DEVICE_WAIT);
+        atomicAdd(&c->bar, kAbortBias);
+        abort = 1;
         break;
       }
-      if (it > 32) __nanosleep(40);
+      if (it > 256) __nanosleep(32);
     }
-    *s_abort = (*(volatile int*)&c->status == (int)S_DEVICE_WAIT);
+    *s_abort = abort;
   }
   __syncthreads();
   return !*s_abort;

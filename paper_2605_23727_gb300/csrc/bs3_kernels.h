@@ -1,9 +1,35 @@
-// Kernel lookup across translation units (one unit per kind compiles in parallel).
+// Generated by gen_inst.py: kernel lookup across translation units.
 #pragma once
 
 namespace bs3 {
-const void* kernel_lco_cfg(int store);
-const void* kernel_lco_paper(int store);
-const void* kernel_kuramoto(int store);
-const void* kernel_circadian(int store);
+const void* kernel_lco_cfg_f64();
+const void* kernel_lco_cfg_f32();
+const void* kernel_lco_cfg_bf16();
+const void* kernel_lco_cfg_f16();
+const void* kernel_lco_cfg_fp8();
+const void* kernel_lco_paper_f64();
+const void* kernel_lco_paper_f32();
+const void* kernel_lco_paper_bf16();
+const void* kernel_lco_paper_f16();
+const void* kernel_lco_paper_fp8();
+const void* kernel_kuramoto_f64();
+const void* kernel_kuramoto_f32();
+const void* kernel_kuramoto_bf16();
+const void* kernel_kuramoto_f16();
+const void* kernel_kuramoto_fp8();
+const void* kernel_circadian_f64();
+const void* kernel_circadian_f32();
+const void* kernel_circadian_bf16();
+const void* kernel_circadian_f16();
+const void* kernel_circadian_fp8();
+
+inline const void* kernel_lookup(int kind, int store) {
+  static const void* (*const table[4][5])() = {
+      {kernel_lco_cfg_f64, kernel_lco_cfg_f32, kernel_lco_cfg_bf16, kernel_lco_cfg_f16, kernel_lco_cfg_fp8},
+      {kernel_lco_paper_f64, kernel_lco_paper_f32, kernel_lco_paper_bf16, kernel_lco_paper_f16, kernel_lco_paper_fp8},
+      {kernel_kuramoto_f64, kernel_kuramoto_f32, kernel_kuramoto_bf16, kernel_kuramoto_f16, kernel_kuramoto_fp8},
+      {kernel_circadian_f64, kernel_circadian_f32, kernel_circadian_bf16, kernel_circadian_f16, kernel_circadian_fp8},
+  };
+  return table[kind][store]();
+}
 }  // namespace bs3

@@ -6,10 +6,13 @@
 //   B3: K3 = f(Y3); X' = X + h(2/9 K1+1/3 K2+4/9 K3) -> j-vector 2  | barrier
 //   B4: K4 = f(X'); E = max_k |h sum e_l K_l| / W_k (grid max)      | barrier
 //   every CTA then takes the same accept/reject decision from E.
-// Each warp owns fixed tiles of RB rows (agents); lane r of the warp owns
-// agent row0 + r for all row-local work (stage combinations, agent term,
-// error, dense output), so only the j-vectors cross CTAs.  The coupling of a
-// stage is an HBM/L2-streaming pass over the stored weights.
+// Each CTA owns a contiguous block of agents (rows) for the whole solve and
+// keeps their state (X, X', K1..K4) and per-agent parameters in shared
+// memory; only the j-vectors (G-precision values of the coupled component)
+// cross CTAs, through global memory between grid barriers.  Inside a CTA,
+// four groups of four warps take row blocks of RB agents; a group streams the
+// RB rows of stored weights from HBM/L2 with 16-byte non-allocating loads,
+// every thread reusing its j-vector chunk over the RB rows.
 #pragma once
 
 #include "bs3_device.cuh"
@@ -45,7 +48,17 @@ struct Args {
   double* out0;
   double* out1;
   long long max_attempts, max_rejects, spin_limit;
+  int rc;                   // rows per CTA capacity (ceil(N / grid))
+  int slab_bytes;           // > 0: each CTA keeps its rc weight rows in shared memory
+  double* hist;             // optional per-attempt records [hist_cap][kHistDoubles]
+  long long hist_cap;
 };
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Prec {
   int f, s, g;  // 0 = S (binary32), 1 = D (binary64)
@@ -95,26 +108,53 @@ __device__ __forceinline__ void put_jv(const Args& a, int buf, int i, const doub
 }
 
 // ---------------------------------------------------------------------------
-// Coupling sums of one warp tile (rows row0 .. row0+RB-1).
+// Accumulator transport between the warps of a group (packed in 64 bits).
 // ---------------------------------------------------------------------------
-template <int ST, int MODE, int NV, int RB>
-__device__ __forceinline__ void gemv_tile(const Args& a, int buf, int row0, int lane, double (&res)[kRBMax][2]) {
+__device__ __forceinline__ unsigned long long pack(const Acc<M_SS>& x) { return (unsigned long long)__float_as_uint(x.s); }
+__device__ __forceinline__ unsigned long long pack(const Acc<M_SD64>& x) { return (unsigned long long)__double_as_longlong(x.s); }
+__device__ __forceinline__ unsigned long long pack(const Acc<M_DD>& x) { return (unsigned long long)__double_as_longlong(x.s); }
+__device__ __forceinline__ unsigned long long pack(const Acc<M_SD2>& x) {
+  return ((unsigned long long)__float_as_uint(x.lo) << 32) | (unsigned long long)__float_as_uint(x.hi);
+}
+__device__ __forceinline__ void merge(Acc<M_SS>& x, unsigned long long b) { x.s = __fadd_rn(x.s, __uint_as_float((unsigned)b)); }
+__device__ __forceinline__ void merge(Acc<M_SD64>& x, unsigned long long b) { x.s = __dadd_rn(x.s, __longlong_as_double((long long)b)); }
+__device__ __forceinline__ void merge(Acc<M_DD>& x, unsigned long long b) { x.s = __dadd_rn(x.s, __longlong_as_double((long long)b)); }
+__device__ __forceinline__ void merge(Acc<M_SD2>& x, unsigned long long b) {
+  const float ohi = __uint_as_float((unsigned)(b & 0xffffffffu)), olo = __uint_as_float((unsigned)(b >> 32));
+  float s, e;
+  two_sum(x.hi, ohi, s, e);
+  x.hi = s;
+  x.lo = __fadd_rn(__fadd_rn(x.lo, olo), e);
+}
+
+__device__ __forceinline__ void group_bar(int g) {
+  asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Coupling partial sums of one row block (rows row0 .. row0+nrows-1) for the
+// columns of thread lt of a 128-thread group; then a warp-level reduction.
+// ---------------------------------------------------------------------------
+template <int ST, int MODE, int NV, int RB, bool RES>
+__device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int lrow0, int nrows, int lt,
+                                         const unsigned char* slab, Acc<MODE> (&acc)[RB][NV]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
   constexpr bool DD = (MODE == M_DD);
-  Acc<MODE> acc[RB][NV];
-  const char* qb = (const char*)a.q;
+  // weights come from the CTA's shared-memory slab (RES) or stream from HBM/L2
+  const char* qb = RES ? (const char*)slab + (size_t)lrow0 * a.ld * L::BYTES
+                       : (const char*)a.q + (size_t)row0 * a.ld * L::BYTES;
   const size_t rstride = (size_t)a.ld * L::BYTES;
-  const int nrows = min(RB, a.N - row0);
   const float* v32 = a.jv32 + (size_t)(buf * 2) * a.ld;
   const double* v64 = a.jv64 + (size_t)(buf * 2) * a.ld;
 #pragma unroll(VEC >= 16 ? 1 : 2)
-  for (int col = lane * VEC; col < a.ld; col += 32 * VEC) {
+  for (int col = lt * VEC; col < a.ld; col += kGroupThreads * VEC) {
     uint4 raw[RB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
-      raw[r] = (r < nrows) ? ld_stream16(qb + (size_t)(row0 + r) * rstride + (size_t)col * L::BYTES)
-                           : make_uint4(0u, 0u, 0u, 0u);
+    for (int r = 0; r < RB; ++r) {
+      const char* p = qb + (size_t)r * rstride + (size_t)col * L::BYTES;
+      raw[r] = (r < nrows) ? (RES ? *reinterpret_cast<const uint4*>(p) : ld_stream16(p)) : make_uint4(0u, 0u, 0u, 0u);
+    }
     if (!DD) {
       float vv[NV][VEC];
 #pragma unroll
@@ -163,23 +203,20 @@ __device__ __forceinline__ void gemv_tile(const Args& a, int buf, int row0, int 
 #pragma unroll
   for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int n = 0; n < NV; ++n) {
+    for (int n = 0; n < NV; ++n)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc[r][n].xor_merge(off);
-      res[r][n] = acc[r][n].value();
-    }
 }
 
 // Circadian interaction: r_i = sum_j q_ij atan(x_j - x_i) (Eq. CC).
 template <int ST, int MODE, int RB>
-__device__ __forceinline__ void cc_tile(const Args& a, int buf, int row0, int lane, double (&res)[kRBMax][2]) {
+__device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nrows, int lt,
+                                       Acc<MODE> (&acc)[RB][1]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
   constexpr bool DD = (MODE == M_DD);
-  Acc<MODE> acc[RB];
   const char* qb = (const char*)a.q;
   const size_t rstride = (size_t)a.ld * L::BYTES;
-  const int nrows = min(RB, a.N - row0);
   const float* v32 = a.jv32 + (size_t)(buf * 2) * a.ld;
   const double* v64 = a.jv64 + (size_t)(buf * 2) * a.ld;
   float xi32[RB];
@@ -190,7 +227,7 @@ __device__ __forceinline__ void cc_tile(const Args& a, int buf, int row0, int la
     xi32[r] = DD ? 0.f : v32[i];
     xi64[r] = DD ? v64[i] : 0.0;
   }
-  for (int col = lane * VEC; col < a.ld; col += 32 * VEC) {
+  for (int col = lt * VEC; col < a.ld; col += kGroupThreads * VEC) {
     uint4 raw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -199,12 +236,20 @@ __device__ __forceinline__ void cc_tile(const Args& a, int buf, int row0, int la
     if (!DD) {
       float xj[VEC];
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) xj[e] = v32[col + e];
+      for (int e = 0; e < VEC; e += 4) {
+        if (VEC >= 4) {
+          const float4 t = *reinterpret_cast<const float4*>(v32 + col + e);
+          xj[e] = t.x; xj[e + 1] = t.y; xj[e + 2] = t.z; xj[e + 3] = t.w;
+        } else {
+          const float2 t = *reinterpret_cast<const float2*>(v32 + col);
+          xj[0] = t.x; xj[VEC > 1 ? 1 : 0] = t.y;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int e = 0; e < VEC; ++e)
-          acc[r].add_f(L::f(raw[r], e), atan_f32(__fsub_rn(xj[e], xi32[r])));
+          acc[r][0].add_f(L::f(raw[r], e), atan_f32(__fsub_rn(xj[e], xi32[r])));
     } else {
       double xj[VEC];
 #pragma unroll
@@ -213,16 +258,13 @@ __device__ __forceinline__ void cc_tile(const Args& a, int buf, int row0, int la
       for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int e = 0; e < VEC; ++e)
-          acc[r].add_d(L::get_d(raw[r], e), atan(__dsub_rn(xj[e], xi64[r])));
+          acc[r][0].add_d(L::get_d(raw[r], e), atan(__dsub_rn(xj[e], xi64[r])));
     }
   }
 #pragma unroll
-  for (int r = 0; r < RB; ++r) {
+  for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[r].xor_merge(off);
-    res[r][0] = acc[r].value();
-    res[r][1] = 0.0;
-  }
+    for (int off = 16; off > 0; off >>= 1) acc[r][0].xor_merge(off);
 }
 
 // ---------------------------------------------------------------------------
@@ -230,49 +272,52 @@ __device__ __forceinline__ void cc_tile(const Args& a, int buf, int row0, int la
 // Y: stage argument of agent i (d values); s0, s1: coupling sums (binary32
 // values when Sigma = S).  Operation order mirrors the definitions exactly.
 // ---------------------------------------------------------------------------
+struct RowPar {
+  float scale;
+  double par, th, rowsum;
+};
+
 template <int KIND>
-__device__ __forceinline__ void finish(const Args& a, int i, const double* Y, double s0, double s1,
+__device__ __forceinline__ void finish(const Args& a, const RowPar& rp, const double* Y, double s0, double s1,
                                        Prec p, bool single, double* K) {
-  const int N = a.N;
-  (void)N;
   if (KIND == K_KURAMOTO) {
     if (p.s == 0) {
-      const float sc = a.scale[i];
+      const float sc = rp.scale;
       const float S = (float)s0 * sc, C = (float)s1 * sc;
       float si, ci;
       if (single) sincosf((float)Y[0], &si, &ci);
       else sincos_f_of_d(Y[0], &si, &ci);
       const float cpl = ci * S - si * C;
-      K[0] = p.f == 0 ? (double)((float)a.par[i] + cpl) : a.par[i] + (double)cpl;
+      K[0] = p.f == 0 ? (double)((float)rp.par + cpl) : rp.par + (double)cpl;
     } else {
-      const double sc = (double)a.scale[i];
+      const double sc = (double)rp.scale;
       const double S = s0 * sc, C = s1 * sc;
       double si, ci;
       sincos(Y[0], &si, &ci);
       const double cpl = ci * S - si * C;
-      K[0] = p.f == 0 ? (double)((float)a.par[i] + (float)cpl) : a.par[i] + cpl;
+      K[0] = p.f == 0 ? (double)((float)rp.par + (float)cpl) : rp.par + cpl;
     }
   } else if (KIND == K_LCO_CFG) {
     double ax;
-    if (p.s == 0) ax = (double)((float)s0 * a.scale[i]);
-    else ax = s0 * (double)a.scale[i];
+    if (p.s == 0) ax = (double)((float)s0 * rp.scale);
+    else ax = s0 * (double)rp.scale;
     if (p.f == 0) {
-      const float w = (float)a.par[i], x = (float)Y[0];
+      const float w = (float)rp.par, x = (float)Y[0];
       K[0] = (double)(float)Y[1];
       K[1] = (double)((-(w * w) * x) + (float)ax);
     } else {
-      const double w = a.par[i];
+      const double w = rp.par;
       K[0] = Y[1];
       K[1] = (-(w * w) * Y[0]) + ax;
     }
   } else if (KIND == K_LCO_PAPER) {
     double cpl;
     if (p.s == 0) {
-      const float mx = (float)s0 * a.scale[i];
-      cpl = (double)(mx - (float)a.rowsum[i] * (float)Y[0]);
+      const float mx = (float)s0 * rp.scale;
+      cpl = (double)(mx - (float)rp.rowsum * (float)Y[0]);
     } else {
-      const double mx = s0 * (double)a.scale[i];
-      cpl = mx - a.rowsum[i] * Y[0];
+      const double mx = s0 * (double)rp.scale;
+      cpl = mx - rp.rowsum * Y[0];
     }
     if (p.f == 0) {
       K[0] = (double)((float)Y[1] + (float)cpl);
@@ -284,21 +329,21 @@ __device__ __forceinline__ void finish(const Args& a, int i, const double* Y, do
   } else {  // circadian
     double cpl;
     if (p.s == 0) {
-      const float th = (float)a.theta_h[i];
+      const float th = (float)rp.th;
       const float x2 = (float)Y[1], x2s = x2 * x2;
       const float pref = ((float)a.g[0] * th * (float)a.g[3]) / (th + x2s * x2s);
-      cpl = (double)(pref * ((float)s0 * a.scale[i]));
+      cpl = (double)(pref * ((float)s0 * rp.scale));
     } else {
-      const double th = a.theta_h[i];
+      const double th = rp.th;
       const double x2 = Y[1], x2s = x2 * x2;
       const double pref = (a.g[0] * th * a.g[3]) / (th + x2s * x2s);
-      cpl = pref * (s0 * (double)a.scale[i]);
+      cpl = pref * (s0 * (double)rp.scale);
     }
     if (p.f == 0) {
       const float x1 = (float)Y[0], x2 = (float)Y[1], x3 = (float)Y[2], x4 = (float)Y[3];
       const float k0 = (float)a.g[0], k2 = (float)a.g[1], k3 = (float)a.g[2], aa = (float)a.g[3];
       const float b = (float)a.g[4], c = (float)a.g[5], eps = (float)a.g[6], I0 = (float)a.g[7];
-      const float k1 = (float)a.par[i], th = (float)a.theta_h[i];
+      const float k1 = (float)rp.par, th = (float)rp.th;
       const float x2s = x2 * x2;
       const float hill = (k0 * th) / (th + x2s * x2s);
       const float F1 = hill * (aa * x1 * x1 + 1.f) - k1 * x1;
@@ -310,7 +355,7 @@ __device__ __forceinline__ void finish(const Args& a, int i, const double* Y, do
       const double x1 = Y[0], x2 = Y[1], x3 = Y[2], x4 = Y[3];
       const double k0 = a.g[0], k2 = a.g[1], k3 = a.g[2], aa = a.g[3];
       const double b = a.g[4], c = a.g[5], eps = a.g[6], I0 = a.g[7];
-      const double k1 = a.par[i], th = a.theta_h[i];
+      const double k1 = rp.par, th = rp.th;
       const double x2s = x2 * x2;
       const double hill = (k0 * th) / (th + x2s * x2s);
       const double F1 = hill * (aa * x1 * x1 + 1.0) - k1 * x1;
@@ -324,17 +369,21 @@ __device__ __forceinline__ void finish(const Args& a, int i, const double* Y, do
 
 // ---------------------------------------------------------------------------
 // Row epilogues of the phases.  One function with a runtime switch keeps the
-// number of template instantiations of the coupling loops small.
+// number of template instantiations of the coupling loops small.  The state
+// of the CTA's agents lives in shared memory: six slots [d][rc] whose roles
+// (X, X', K1..K4) rotate on accepted steps.
 // ---------------------------------------------------------------------------
 enum Phase { PH_RHS = 0, PH_K1 = 1, PH_F1 = 2, PH_B2 = 3, PH_B3 = 4, PH_B4 = 5 };
 
 struct Ctx {
-  double* X;
-  double* Xn;
-  double* K1;
-  double* K2;
-  double* K3;
-  double* K4;
+  const unsigned char* slab;  // shared-memory copy of this CTA's weight rows (or null)
+  double* S;          // shared state slots
+  double* spar;       // shared per-agent omega_i / k1_i
+  double* sth;        // shared k1/(k0-k1)
+  double* srs;        // shared row sums
+  float* sscale;      // shared row scales
+  int rc, rb, nr;
+  int iX, iXn, iK1, iK2, iK3, iK4;
   double c21, c32, hs, h0s, thr, rtol;
   Prec p;    // precision of the stage being evaluated
   Prec pn;   // G precision of the next j-vector
@@ -356,24 +405,29 @@ __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff800
 __device__ __forceinline__ double max_nan(double m, double v) { return (v != v || m != m) ? nan_d() : fmax(m, v); }
 
 template <int KIND>
-__device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i, double s0, double s1) {
+__device__ __forceinline__ double& sv(const Ctx& x, int slot, int c, int li) {
+  return x.S[(slot * Dim<KIND>::d + c) * x.rc + li];
+}
+
+template <int KIND>
+__device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int li, double s0, double s1) {
   constexpr int d = Dim<KIND>::d;
   const int N = a.N;
+  const int i = x.rb + li;
+  const RowPar rp{x.sscale[li], x.spar[li], x.sth[li], x.srs[li]};
   double Y[d], K[d];
-  // stage argument of this agent
 #pragma unroll
   for (int c = 0; c < d; ++c) {
-    const int o = c * N + i;
+    const double xo = sv<KIND>(x, x.iX, c, li);
     switch (phase) {
-      case PH_RHS: Y[c] = x.single ? (double)(float)x.X[o] : x.X[o]; break;
-      case PH_K1: Y[c] = x.X[o]; break;
-      case PH_F1: Y[c] = axpy_state(x.X[o], x.h0s, x.K1[o], x.single); break;
-      case PH_B2: Y[c] = axpy_state(x.X[o], x.c21, x.K1[o], x.single); break;
-      case PH_B3: Y[c] = axpy_state(x.X[o], x.c32, x.K2[o], x.single); break;
-      default: Y[c] = x.Xn[o]; break;
+      case PH_F1: Y[c] = axpy_state(xo, x.h0s, sv<KIND>(x, x.iK1, c, li), x.single); break;
+      case PH_B2: Y[c] = axpy_state(xo, x.c21, sv<KIND>(x, x.iK1, c, li), x.single); break;
+      case PH_B3: Y[c] = axpy_state(xo, x.c32, sv<KIND>(x, x.iK2, c, li), x.single); break;
+      case PH_B4: Y[c] = sv<KIND>(x, x.iXn, c, li); break;
+      default: Y[c] = xo; break;   // PH_RHS, PH_K1
     }
   }
-  finish<KIND>(a, i, Y, s0, s1, x.p, x.single, K);
+  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K);
   switch (phase) {
     case PH_RHS:
 #pragma unroll
@@ -382,7 +436,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
     case PH_K1:
 #pragma unroll
       for (int c = 0; c < d; ++c) {
-        x.K1[c * N + i] = K[c];
+        sv<KIND>(x, x.iK1, c, li) = K[c];
         const double sc = x.rtol * fmax(fabs(Y[c]), x.thr);
         x.m0 = max_nan(x.m0, fabs(Y[c]) / sc);
         x.m1 = max_nan(x.m1, fabs(K[c]) / sc);
@@ -391,24 +445,24 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
     case PH_F1:
 #pragma unroll
       for (int c = 0; c < d; ++c) {
-        const double sc = x.rtol * fmax(fabs(x.X[c * N + i]), x.thr);
-        x.m0 = max_nan(x.m0, fabs(K[c] - x.K1[c * N + i]) / sc);
+        const double sc = x.rtol * fmax(fabs(sv<KIND>(x, x.iX, c, li)), x.thr);
+        x.m0 = max_nan(x.m0, fabs(K[c] - sv<KIND>(x, x.iK1, c, li)) / sc);
       }
       break;
     case PH_B2:
 #pragma unroll
       for (int c = 0; c < d; ++c) {
-        x.K2[c * N + i] = K[c];
-        Y[c] = axpy_state(x.X[c * N + i], x.c32, K[c], x.single);
+        sv<KIND>(x, x.iK2, c, li) = K[c];
+        Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c32, K[c], x.single);
       }
       put_jv<KIND>(a, 1, i, Y, x.pn.g, x.single);
       break;
     case PH_B3:
 #pragma unroll
       for (int c = 0; c < d; ++c) {
-        const int o = c * N + i;
-        x.K3[o] = K[c];
-        const double k1 = x.K1[o], k2 = x.K2[o], k3 = K[c], xo = x.X[o];
+        sv<KIND>(x, x.iK3, c, li) = K[c];
+        const double k1 = sv<KIND>(x, x.iK1, c, li), k2 = sv<KIND>(x, x.iK2, c, li), k3 = K[c];
+        const double xo = sv<KIND>(x, x.iX, c, li);
         double xn;
         if (x.single) {
           const float cmb = ((float)kB1 * (float)k1 + (float)kB2 * (float)k2) + (float)kB3 * (float)k3;
@@ -416,7 +470,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
         } else {
           xn = xo + x.hs * ((kB1 * k1 + kB2 * k2) + kB3 * k3);
         }
-        x.Xn[o] = xn;
+        sv<KIND>(x, x.iXn, c, li) = xn;
         Y[c] = xn;
       }
       put_jv<KIND>(a, 2, i, Y, x.pn.g, x.single);
@@ -424,9 +478,9 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
     default:  // PH_B4: K4 and the error of Eq. ERROR-O23
 #pragma unroll
       for (int c = 0; c < d; ++c) {
-        const int o = c * N + i;
-        x.K4[o] = K[c];
-        const double k1 = x.K1[o], k2 = x.K2[o], k3 = x.K3[o], k4 = K[c];
+        sv<KIND>(x, x.iK4, c, li) = K[c];
+        const double k1 = sv<KIND>(x, x.iK1, c, li), k2 = sv<KIND>(x, x.iK2, c, li);
+        const double k3 = sv<KIND>(x, x.iK3, c, li), k4 = K[c];
         double dv;
         if (x.single) {
           const float cmb = (((float)kE1 * (float)k1 + (float)kE2 * (float)k2) + (float)kE3 * (float)k3) +
@@ -435,7 +489,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
         } else {
           dv = x.hs * (((kE1 * k1 + kE2 * k2) + kE3 * k3) + kE4 * k4);
         }
-        const double w = fmax(fmax(fabs(x.X[o]), fabs(Y[c])), x.thr);
+        const double w = fmax(fmax(fabs(sv<KIND>(x, x.iX, c, li)), fabs(Y[c])), x.thr);
         double v = fabs(dv) / w;
         if (!isfinite(Y[c]) || !isfinite(k4)) v = nan_d();
         x.m1 = max_nan(x.m1, v);
@@ -445,35 +499,60 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int i
 }
 
 // ---------------------------------------------------------------------------
-// One stage: coupling sums of every tile of this warp, then the row epilogue.
+// One stage over the CTA's agents: row blocks of RB agents go to the four
+// warp groups; each group reduces its partial sums through shared memory
+// and the first RB threads of the group run the epilogues.
 // ---------------------------------------------------------------------------
-template <int KIND, int ST, int MODE>
-__device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int buf, int gw, int tw, int lane) {
+template <int KIND, int ST, int MODE, bool RES>
+__device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
   constexpr int RB = rows_per_tile(KIND);
-  const int ntiles = (a.N + RB - 1) / RB;
-  for (int tile = gw; tile < ntiles; tile += tw) {
-    const int row0 = tile * RB;
-    double res[kRBMax][2];
-    if (KIND == K_CIRCADIAN) cc_tile<ST, MODE, RB>(a, buf, row0, lane, res);
-    else if (KIND == K_KURAMOTO) gemv_tile<ST, MODE, 2, RB>(a, buf, row0, lane, res);
-    else gemv_tile<ST, MODE, 1, RB>(a, buf, row0, lane, res);
-    double s0 = 0.0, s1 = 0.0;
+  constexpr int NV = (KIND == K_KURAMOTO) ? 2 : 1;
+  const int g = threadIdx.x / kGroupThreads, lt = threadIdx.x % kGroupThreads;
+  const int wig = lt >> 5, lane = lt & 31;
+  const int nrb = (x.nr + RB - 1) / RB;
+  for (int rbk = g; rbk < nrb; rbk += kGroups) {
+    const int lrow0 = rbk * RB;
+    const int nrows = min(RB, x.nr - lrow0);
+    Acc<MODE> acc[RB][NV];
+    if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, (Acc<MODE>(&)[RB][1])acc);
+    else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, x.slab, acc);
+    if (lane == 0) {
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
-      if (lane == r) { s0 = res[r][0]; s1 = (KIND == K_KURAMOTO) ? res[r][1] : 0.0; }
-    const int i = row0 + lane;
-    if (lane < RB && i < a.N) epilogue<KIND>(a, x, phase, i, s0, s1);
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int n = 0; n < NV; ++n) red[((g * 4 + wig) * kRBMax + r) * 2 + n] = pack(acc[r][n]);
+    }
+    group_bar(g);
+    if (lt < nrows) {
+      double s[2] = {0.0, 0.0};
+#pragma unroll
+      for (int n = 0; n < NV; ++n) {
+        Acc<MODE> tot;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) merge(tot, red[((g * 4 + w) * kRBMax + lt) * 2 + n]);
+        s[n] = tot.value();
+      }
+      epilogue<KIND>(a, x, phase, lrow0 + lt, s[0], s[1]);
+    }
+    group_bar(g);
   }
 }
 
-template <int KIND, int ST>
-__device__ __forceinline__ void stage(const Args& a, Ctx& x, int phase, int buf, int gw, int tw, int lane) {
+template <int KIND, int ST, bool RES>
+__device__ __forceinline__ void stage_r(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
   switch (sum_mode(x.p, a.accum)) {
-    case M_SS: stage_m<KIND, ST, M_SS>(a, x, phase, buf, gw, tw, lane); break;
-    case M_SD64: stage_m<KIND, ST, M_SD64>(a, x, phase, buf, gw, tw, lane); break;
-    case M_SD2: stage_m<KIND, ST, M_SD2>(a, x, phase, buf, gw, tw, lane); break;
-    default: stage_m<KIND, ST, M_DD>(a, x, phase, buf, gw, tw, lane); break;
+    case M_SS: stage_m<KIND, ST, M_SS, RES>(a, x, phase, buf, red); break;
+    case M_SD64: stage_m<KIND, ST, M_SD64, RES>(a, x, phase, buf, red); break;
+    case M_SD2: stage_m<KIND, ST, M_SD2, RES>(a, x, phase, buf, red); break;
+    default: stage_m<KIND, ST, M_DD, RES>(a, x, phase, buf, red); break;
   }
+}
+
+// The circadian interaction is ALU-bound and always streams its weights.
+template <int KIND, int ST>
+__device__ __forceinline__ void stage(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
+  if (KIND != K_CIRCADIAN && x.slab != nullptr) stage_r<KIND, ST, (KIND != K_CIRCADIAN)>(a, x, phase, buf, red);
+  else stage_r<KIND, ST, false>(a, x, phase, buf, red);
 }
 
 // Block-wide max of non-negative binary64 values (bit patterns), then one
@@ -501,241 +580,341 @@ __device__ __forceinline__ double ld_bits(const unsigned long long* p) {
   return __longlong_as_double((long long)__ldcg(p));
 }
 
+// Shared-memory bytes of a launch: six state slots [d][rc] plus per-agent
+// parameters (three binary64 and one binary32 per agent).
+__host__ __device__ constexpr size_t state_smem_bytes(int d, int rc) {
+  return (size_t)rc * (6 * d * 8 + 3 * 8 + 4) + 16;
+}
+
+
+// Scalar control of a solve, computed by thread 0 of every CTA (all CTAs
+// compute identical values from identical inputs) and broadcast through
+// shared memory: binary64 is scarce on this GPU, so no other thread repeats it.
+constexpr int kThetaMax = 32;
+struct Scal {
+  double t, h, hs, c21, c32, E, hstep, tstep0;
+  long long n_acc, n_rej, n_rhs, next_out, out_end;
+  int status, last, stop, accepted, rejected, parity;
+  double theta[kThetaMax];
+};
+
 template <int KIND, int ST>
 __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   constexpr int d = Dim<KIND>::d;
-  constexpr int RB = rows_per_tile(KIND);
+  extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ int s_abort;
   __shared__ unsigned long long s_red[kBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-  // tile t belongs to CTA t % grid: consecutive tiles land on different SMs
-  const int gw = warp * gridDim.x + blockIdx.x, tw = gridDim.x * nw;
+  __shared__ unsigned long long s_grp[kGroups * 4 * kRBMax * 2];
+  __shared__ Scal sc;
   const int N = a.N;
-  const int ntiles = (N + RB - 1) / RB;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x;
   Control* ctrl = a.ctrl;
   unsigned long long bt = 0;
-  if (threadIdx.x == 0) s_abort = 0;
+  if (tid == 0) s_abort = 0;
 
   Ctx x;
-  x.X = a.X; x.Xn = a.Xn;
-  x.K1 = a.Kb[0]; x.K2 = a.Kb[1]; x.K3 = a.Kb[2]; x.K4 = a.Kb[3];
+  x.rc = a.rc;
+  x.rb = (int)(((long long)b * N) / G);
+  x.nr = (int)(((long long)(b + 1) * N) / G) - x.rb;
+  x.slab = a.slab_bytes > 0 ? dyn : nullptr;
+  x.S = (double*)(dyn + a.slab_bytes);
+  x.spar = x.S + 6 * d * x.rc;
+  x.sth = x.spar + x.rc;
+  x.srs = x.sth + x.rc;
+  x.sscale = (float*)(x.srs + x.rc);
+  x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
   x.rtol = a.rtol;
   x.thr = a.atol / a.rtol;
   x.m0 = 0.0; x.m1 = 0.0;
   x.c21 = x.c32 = x.hs = x.h0s = 0.0;
+  x.single = (a.job == JOB_RHS) ? (a.rhs_f == 0 && a.rhs_s == 0 && a.rhs_g == 0) : (a.variant == V_SINGLE);
+  const bool single = x.single;
+
+  // this CTA's weight rows into shared memory (contiguous in the [N][ld] layout)
+  if (a.slab_bytes > 0) {
+    const size_t eb = (size_t)KLoad<ST>::BYTES;
+    const uint4* src = reinterpret_cast<const uint4*>((const char*)a.q + (size_t)x.rb * a.ld * eb);
+    uint4* dst = reinterpret_cast<uint4*>(dyn);
+    const int n16 = (int)((size_t)x.nr * a.ld * eb / 16);
+    for (int e = tid; e < n16; e += blockDim.x) dst[e] = ld_stream16(src + e);
+  }
+  // per-agent parameters and the initial state of this CTA's agents
+  for (int li = tid; li < x.nr; li += blockDim.x) {
+    const int i = x.rb + li;
+    x.spar[li] = a.par[i];
+    x.sth[li] = a.theta_h ? a.theta_h[i] : 0.0;
+    x.srs[li] = a.rowsum[i];
+    x.sscale[li] = a.scale[i];
+#pragma unroll
+    for (int c = 0; c < d; ++c) {
+      const double y = a.X[c * N + i];
+      if (a.job == JOB_SOLVE)
+        for (long long k = 0; k < a.n_out && a.t_out[k] <= a.t0; ++k) a.y_out[(size_t)k * d * N + c * N + i] = y;
+      sv<KIND>(x, x.iX, c, li) = single ? (double)(float)y : y;
+      if (a.job == JOB_ATTEMPT) {
+        const double k1 = a.Kb[0][c * N + i];
+        sv<KIND>(x, x.iK1, c, li) = single ? (double)(float)k1 : k1;
+      }
+    }
+  }
+  __syncthreads();
 
   // -------------------------------------------------------------------- RHS
   if (a.job == JOB_RHS) {
     x.p = Prec{a.rhs_f, a.rhs_s, a.rhs_g};
-    x.single = (a.rhs_f == 0 && a.rhs_s == 0 && a.rhs_g == 0);
-    for (int tile = gw; tile < ntiles; tile += tw) {
-      const int i = tile * RB + lane;
-      if (!(lane < RB && i < N)) continue;
+    for (int li = tid; li < x.nr; li += blockDim.x) {
       double Y[d];
 #pragma unroll
-      for (int c = 0; c < d; ++c) Y[c] = x.single ? (double)(float)x.X[c * N + i] : x.X[c * N + i];
-      put_jv<KIND>(a, 0, i, Y, x.p.g, x.single);
+      for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
+      put_jv<KIND>(a, 0, x.rb + li, Y, x.p.g, single);
     }
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) return;
-    stage<KIND, ST>(a, x, PH_RHS, 0, gw, tw, lane);
+    stage<KIND, ST>(a, x, PH_RHS, 0, s_grp);
     return;
   }
 
-  x.single = (a.variant == V_SINGLE);
-  const bool single = x.single;
   const Prec p2 = variant_prec(a.variant, 2);
   const Prec p3 = variant_prec(a.variant, 3);
   const Prec p4 = variant_prec(a.variant, 4);
   const double rtol = a.rtol;
 
-  double t = a.t0, h = a.h_given;
-  long long n_acc = 0, n_rej = 0, n_rhs = 0, next_out = 0;
-  int status = S_OK;
-  int parity = 0;
-  bool rejected_this_step = false;
+  if (tid == 0) {
+    sc.t = a.t0; sc.h = a.h_given; sc.E = 0.0;
+    sc.n_acc = 0; sc.n_rej = 0; sc.n_rhs = 0; sc.next_out = 0; sc.out_end = 0;
+    sc.status = S_OK; sc.last = 0; sc.stop = 0; sc.accepted = 0; sc.rejected = 0; sc.parity = 0;
+    if (a.job == JOB_SOLVE)
+      while (sc.next_out < a.n_out && a.t_out[sc.next_out] <= a.t0) ++sc.next_out;
+  }
 
-  // ------------------------------------------------------------ set-up rows
-  for (int tile = gw; tile < ntiles; tile += tw) {
-    const int i = tile * RB + lane;
-    if (!(lane < RB && i < N)) continue;
-    if (a.job == JOB_SOLVE) {
-      for (long long k = 0; k < a.n_out && a.t_out[k] <= a.t0; ++k)
-#pragma unroll
-        for (int c = 0; c < d; ++c) a.y_out[(size_t)k * d * N + c * N + i] = x.X[c * N + i];
-    }
-    if (single) {
-#pragma unroll
-      for (int c = 0; c < d; ++c) {
-        x.X[c * N + i] = (double)(float)x.X[c * N + i];
-        if (a.job == JOB_ATTEMPT) x.K1[c * N + i] = (double)(float)x.K1[c * N + i];
-      }
-    }
-    if (a.job == JOB_SOLVE) {
+  if (a.job == JOB_SOLVE) {
+    for (int li = tid; li < x.nr; li += blockDim.x) {
       double Y[d];
 #pragma unroll
-      for (int c = 0; c < d; ++c) Y[c] = x.X[c * N + i];
-      put_jv<KIND>(a, 0, i, Y, p4.g, single);
+      for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
+      put_jv<KIND>(a, 0, x.rb + li, Y, p4.g, single);
     }
   }
-  if (a.job == JOB_SOLVE)
-    while (next_out < a.n_out && a.t_out[next_out] <= a.t0) ++next_out;
-
   if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
 
   if (a.job == JOB_SOLVE) {
     // ---- K1 = f(t0, y0) with the k4 row; starting-step norms d0, d1
     x.p = p4;
     x.m0 = 0.0; x.m1 = 0.0;
-    stage<KIND, ST>(a, x, PH_K1, 0, gw, tw, lane);
+    stage<KIND, ST>(a, x, PH_K1, 0, s_grp);
     block_max(x.m0, &ctrl->red[0], s_red);
     block_max(x.m1, &ctrl->red[1], s_red);
-    n_rhs = 1;
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
-    {
-      const double d0c = ld_bits(&ctrl->red[0]);
-      const double d1c = ld_bits(&ctrl->red[1]);
-      if (d0c != d0c || isinf(d0c) || d1c != d1c || isinf(d1c)) { status = S_NONFINITE; goto finish_up; }
-    }
-    if (!(a.h_given > 0.0)) {
+    if (tid == 0) {
+      sc.n_rhs = 1;
       const double d0 = ld_bits(&ctrl->red[0]);
       const double d1 = ld_bits(&ctrl->red[1]);
+      if (d0 != d0 || isinf(d0) || d1 != d1 || isinf(d1)) sc.status = S_NONFINITE;
       const double h0 = (d0 >= 1e-5 && d1 >= 1e-5) ? 0.01 * d0 / d1 : 1e-6;
-      x.h0s = single ? (double)(float)h0 : h0;
-      // y1 = y0 + h0 f0 -> j-vector 1
-      for (int tile = gw; tile < ntiles; tile += tw) {
-        const int i = tile * RB + lane;
-        if (!(lane < RB && i < N)) continue;
+      sc.hs = h0;
+      sc.c21 = single ? (double)(float)h0 : h0;   // y1 = y0 + h0 f0 in the state precision
+    }
+    __syncthreads();
+    if (sc.status != S_OK) goto finish_up;
+    if (!(a.h_given > 0.0)) {
+      x.h0s = sc.c21;
+      for (int li = tid; li < x.nr; li += blockDim.x) {
         double Y[d];
 #pragma unroll
-        for (int c = 0; c < d; ++c) Y[c] = axpy_state(x.X[c * N + i], x.h0s, x.K1[c * N + i], single);
-        put_jv<KIND>(a, 1, i, Y, p4.g, single);
+        for (int c = 0; c < d; ++c)
+          Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.h0s, sv<KIND>(x, x.iK1, c, li), single);
+        put_jv<KIND>(a, 1, x.rb + li, Y, p4.g, single);
       }
       if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
       x.m0 = 0.0;
-      stage<KIND, ST>(a, x, PH_F1, 1, gw, tw, lane);
+      stage<KIND, ST>(a, x, PH_F1, 1, s_grp);
       block_max(x.m0, &ctrl->red[2], s_red);
-      n_rhs = 2;
       if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
-      const double d2 = ld_bits(&ctrl->red[2]) / h0;
-      const double m = fmax(d1, d2);
-      const double h1 = (m > 1e-15) ? pow(0.01 / m, 1.0 / 3.0) : fmax(1e-6, h0 * 1e-3);
-      h = fmin(fmin(100.0 * h0, h1), a.hmax);
+      if (tid == 0) {
+        sc.n_rhs = 2;
+        const double h0 = sc.hs;
+        const double d1 = ld_bits(&ctrl->red[1]);
+        const double d2 = ld_bits(&ctrl->red[2]) / h0;
+        const double m = fmax(d1, d2);
+        const double h1 = (m > 1e-15) ? pow(0.01 / m, 1.0 / 3.0) : fmax(1e-6, h0 * 1e-3);
+        sc.h = fmin(fmin(100.0 * h0, h1), a.hmax);
+      }
     }
   }
 
   while (true) {
-    bool last = false;
-    if (a.job == JOB_SOLVE) {
-      if (!(t < a.t1)) break;
-      if (n_rej > a.max_rejects) { status = S_MAX_REJECTS; break; }
-      if (n_acc + n_rej >= a.max_attempts) { status = S_MAX_STEPS; break; }
-      if (n_acc + n_rej > 0 && __ldcg(&ctrl->cancel_seen[parity ^ 1])) { status = S_TIMEOUT; break; }
-      h = fmin(h, a.hmax);
-      if (h <= a.hmin) { status = S_STEP_TOO_SMALL; break; }
-      last = (t + 1.1 * h >= a.t1);
-      if (last) h = a.t1 - t;
+    // ---- per-attempt scalars (thread 0), then A: Y2 -> j-vector 0
+    __syncthreads();
+    if (tid == 0) {
+      const long long na = sc.n_acc + sc.n_rej;
+      sc.stop = 0;
+      if (a.job == JOB_SOLVE) {
+        if (!(sc.t < a.t1)) sc.stop = 1;
+        else if (sc.n_rej > a.max_rejects) { sc.status = S_MAX_REJECTS; sc.stop = 1; }
+        else if (na >= a.max_attempts) { sc.status = S_MAX_STEPS; sc.stop = 1; }
+        else if (na > 0 && __ldcg(&ctrl->cancel_seen[sc.parity ^ 1])) { sc.status = S_TIMEOUT; sc.stop = 1; }
+        else {
+          double h = fmin(sc.h, a.hmax);
+          if (h <= a.hmin) { sc.status = S_STEP_TOO_SMALL; sc.stop = 1; }
+          sc.last = (sc.t + 1.1 * h >= a.t1);
+          if (sc.last) h = a.t1 - sc.t;
+          sc.h = h;
+        }
+      } else if (na > 0) {
+        sc.stop = 1;
+      }
+      const double h = sc.h;
+      sc.hs = single ? (double)(float)h : h;
+      sc.c21 = single ? (double)(0.5f * (float)h) : 0.5 * h;
+      sc.c32 = single ? (double)(0.75f * (float)h) : 0.75 * h;
     }
-    x.hs = single ? (double)(float)h : h;
-    x.c21 = single ? (double)(0.5f * (float)h) : 0.5 * h;
-    x.c32 = single ? (double)(0.75f * (float)h) : 0.75 * h;
-    // ---- A: Y2 -> j-vector 0
-    for (int tile = gw; tile < ntiles; tile += tw) {
-      const int i = tile * RB + lane;
-      if (!(lane < RB && i < N)) continue;
+    __syncthreads();
+    if (sc.stop) break;
+    const bool rec = (a.hist != nullptr) && b == 0 && tid == 0 && (sc.n_acc + sc.n_rej) < a.hist_cap;
+    unsigned long long ts[5];
+    if (rec) ts[0] = globaltimer_ns();
+    x.hs = sc.hs;
+    x.c21 = sc.c21;
+    x.c32 = sc.c32;
+    const int parity = sc.parity;
+    for (int li = tid; li < x.nr; li += blockDim.x) {
       double Y[d];
 #pragma unroll
-      for (int c = 0; c < d; ++c) Y[c] = axpy_state(x.X[c * N + i], x.c21, x.K1[c * N + i], single);
-      put_jv<KIND>(a, 0, i, Y, p2.g, single);
+      for (int c = 0; c < d; ++c)
+        Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
+      put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
     }
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (rec) ts[1] = globaltimer_ns();
     // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->emax[parity ^ 1] = 0ull;
+    if (b == 0 && tid == 0) ctrl->emax[parity ^ 1] = 0ull;
     x.p = p2; x.pn = p3;
-    stage<KIND, ST>(a, x, PH_B2, 0, gw, tw, lane);
+    stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (rec) ts[2] = globaltimer_ns();
     // ---- B3: K3 = f(Y3); X' -> j-vector 2
     x.p = p3; x.pn = p4;
-    stage<KIND, ST>(a, x, PH_B3, 1, gw, tw, lane);
+    stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (rec) ts[3] = globaltimer_ns();
     // ---- B4: K4 = f(X'); error norm
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (b == 0 && tid == 0) {
       ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
-      if (a.progress) *a.progress = t;
+      if (a.progress) *a.progress = sc.t;
     }
     x.p = p4;
     x.m1 = 0.0;
-    stage<KIND, ST>(a, x, PH_B4, 2, gw, tw, lane);
+    stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
     block_max(x.m1, &ctrl->emax[parity], s_red);
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
-    n_rhs += 3;
-    const double E = ld_bits(&ctrl->emax[parity]);
+    // ---- decision (thread 0)
+    if (tid == 0) {
+      const double E = ld_bits(&ctrl->emax[parity]);
+      sc.E = E;
+      sc.n_rhs += 3;
+      if (rec) {
+        ts[4] = globaltimer_ns();
+        double* r = a.hist + (size_t)(sc.n_acc + sc.n_rej) * kHistDoubles;
+        r[0] = sc.t; r[1] = sc.h; r[2] = E; r[3] = (E <= rtol) ? 1.0 : 0.0;
+        for (int k = 1; k < 5; ++k) r[3 + k] = (double)(ts[k] - ts[0]);
+      }
+      sc.accepted = 0;
+      if (a.job == JOB_ATTEMPT) {
+        ++sc.n_acc;
+      } else if (E != E || isinf(E)) {
+        sc.status = S_NONFINITE;
+        ++sc.n_rej;
+      } else if (E <= rtol) {
+        const double h = sc.h;
+        const double t_new = sc.last ? a.t1 : sc.t + h;
+        sc.hstep = h;
+        sc.tstep0 = sc.t;
+        long long e = sc.next_out;
+        while (e < a.n_out && a.t_out[e] <= t_new && e - sc.next_out < kThetaMax) {
+          sc.theta[e - sc.next_out] = (a.t_out[e] - sc.t) / h;
+          ++e;
+        }
+        sc.out_end = e;
+        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * pow(rtol / E, 1.0 / 3.0));
+        if (sc.rejected) fac = fmin(1.0, fac);
+        sc.h = h * fac;
+        sc.t = t_new;
+        ++sc.n_acc;
+        sc.rejected = 0;
+        sc.accepted = 1;
+      } else {
+        ++sc.n_rej;
+        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * pow(rtol / E, 1.0 / 3.0));
+        sc.rejected = 1;
+      }
+      sc.parity ^= 1;
+    }
+    __syncthreads();
     if (a.job == JOB_ATTEMPT) {
-      for (int tile = gw; tile < ntiles; tile += tw) {
-        const int i = tile * RB + lane;
-        if (!(lane < RB && i < N)) continue;
+      for (int li = tid; li < x.nr; li += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < d; ++c) {
-          a.out0[c * N + i] = x.Xn[c * N + i];
-          a.out1[c * N + i] = x.K4[c * N + i];
+          a.out0[c * N + x.rb + li] = sv<KIND>(x, x.iXn, c, li);
+          a.out1[c * N + x.rb + li] = sv<KIND>(x, x.iK4, c, li);
         }
       }
       break;
     }
-    if (E != E || isinf(E)) { status = S_NONFINITE; ++n_rej; break; }
-    if (E <= rtol) {
-      const double t_new = last ? a.t1 : t + h;
-      while (next_out < a.n_out && a.t_out[next_out] <= t_new) {
-        const double th = (a.t_out[next_out] - t) / h;
-        for (int tile = gw; tile < ntiles; tile += tw) {
-          const int i = tile * RB + lane;
-          if (!(lane < RB && i < N)) continue;
+    if (sc.status != S_OK) break;
+    if (sc.accepted) {
+      // dense output: cubic Hermite on (t_n, X, K1), (t_n + h, X', K4)
+      while (true) {
+        const long long k0 = sc.next_out, k1 = sc.out_end;
+        if (k0 >= k1) break;
+        const double hstep = sc.hstep;
+        for (long long k = k0; k < k1; ++k) {
+          const double th = sc.theta[k - k0];
+          for (int li = tid; li < x.nr; li += blockDim.x) {
 #pragma unroll
-          for (int c = 0; c < d; ++c) {
-            const int o = c * N + i;
-            const double y0 = x.X[o], y1 = x.Xn[o], f0 = x.K1[o], f1 = x.K4[o];
-            a.y_out[(size_t)next_out * d * N + o] =
-                ((1.0 - th) * y0 + th * y1) +
-                (th * (th - 1.0)) * (((1.0 - 2.0 * th) * (y1 - y0) + ((th - 1.0) * h) * f0) + (th * h) * f1);
+            for (int c = 0; c < d; ++c) {
+              const double y0 = sv<KIND>(x, x.iX, c, li), y1 = sv<KIND>(x, x.iXn, c, li);
+              const double f0 = sv<KIND>(x, x.iK1, c, li), f1 = sv<KIND>(x, x.iK4, c, li);
+              a.y_out[(size_t)k * d * N + c * N + x.rb + li] =
+                  ((1.0 - th) * y0 + th * y1) +
+                  (th * (th - 1.0)) * (((1.0 - 2.0 * th) * (y1 - y0) + ((th - 1.0) * hstep) * f0) + (th * hstep) * f1);
+            }
           }
         }
-        ++next_out;
+        __syncthreads();
+        if (tid == 0) {
+          sc.next_out = k1;
+          // more outputs inside this step than fit in one batch
+          const double t_step0 = sc.tstep0;
+          long long e = k1;
+          while (e < a.n_out && a.t_out[e] <= sc.t && e - k1 < kThetaMax) {
+            sc.theta[e - k1] = (a.t_out[e] - t_step0) / hstep;
+            ++e;
+          }
+          sc.out_end = e;
+        }
+        __syncthreads();
       }
-      double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * pow(rtol / E, 1.0 / 3.0));
-      if (rejected_this_step) fac = fmin(1.0, fac);
-      const double h_new = h * fac;
-      t = t_new;
-      double* tmp = x.X; x.X = x.Xn; x.Xn = tmp;
-      tmp = x.K1; x.K1 = x.K4; x.K4 = tmp;
-      ++n_acc;
-      rejected_this_step = false;
-      h = h_new;
-    } else {
-      ++n_rej;
-      if (!rejected_this_step) h = h * fmax(0.5, 0.8 * pow(rtol / E, 1.0 / 3.0));
-      else h = h * 0.5;
-      rejected_this_step = true;
+      int tmp = x.iX; x.iX = x.iXn; x.iXn = tmp;
+      tmp = x.iK1; x.iK1 = x.iK4; x.iK4 = tmp;
     }
-    parity ^= 1;
   }
 
 finish_up:
+  __syncthreads();
   if (a.job == JOB_SOLVE && a.final_y != nullptr && !s_abort) {
-    for (int tile = gw; tile < ntiles; tile += tw) {
-      const int i = tile * RB + lane;
-      if (!(lane < RB && i < N)) continue;
+    for (int li = tid; li < x.nr; li += blockDim.x) {
 #pragma unroll
-      for (int c = 0; c < d; ++c) a.final_y[c * N + i] = x.X[c * N + i];
+      for (int c = 0; c < d; ++c) a.final_y[c * N + x.rb + li] = sv<KIND>(x, x.iX, c, li);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (status != S_OK) atomicCAS(&ctrl->status, 0, status);
-    ctrl->n_acc = n_acc;
-    ctrl->n_rej = n_rej;
-    ctrl->n_rhs = n_rhs;
-    ctrl->n_out = next_out;
-    ctrl->t = t;
-    ctrl->h = h;
+  if (b == 0 && tid == 0) {
+    if (sc.status != S_OK) atomicCAS(&ctrl->status, 0, sc.status);
+    ctrl->n_acc = sc.n_acc;
+    ctrl->n_rej = sc.n_rej;
+    ctrl->n_rhs = sc.n_rhs;
+    ctrl->n_out = sc.next_out;
+    ctrl->t = sc.t;
+    ctrl->h = sc.h;
   }
 }
 

@@ -1,0 +1,30 @@
+"""Writes one translation unit per (kind, stored type) solver kernel so that
+nvcc can compile them in parallel.  Run: python gen_inst.py"""
+
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+KINDS = [("lco_cfg", "K_LCO_CFG"), ("lco_paper", "K_LCO_PAPER"), ("kuramoto", "K_KURAMOTO"),
+         ("circadian", "K_CIRCADIAN")]
+STORES = [("f64", "ST_F64"), ("f32", "ST_F32"), ("bf16", "ST_BF16"), ("f16", "ST_F16"), ("fp8", "ST_FP8")]
+
+for kname, kenum in KINDS:
+    for sname, senum in STORES:
+        with open(os.path.join(HERE, f"inst_{kname}_{sname}.cu"), "w") as fh:
+            fh.write(f"// Generated by gen_inst.py: solver kernel for {kname} with {sname} weights.\n"
+                     f'#include "bs3_solver.cuh"\n\n'
+                     f"namespace bs3 {{\n"
+                     f"const void* kernel_{kname}_{sname}() {{ return (const void*)bs3_kernel<{kenum}, {senum}>; }}\n"
+                     f"}}  // namespace bs3\n")
+
+with open(os.path.join(HERE, "bs3_kernels.h"), "w") as fh:
+    fh.write("// Generated by gen_inst.py: kernel lookup across translation units.\n#pragma once\n\n"
+             "namespace bs3 {\n")
+    for kname, _ in KINDS:
+        for sname, _ in STORES:
+            fh.write(f"const void* kernel_{kname}_{sname}();\n")
+    fh.write("\ninline const void* kernel_lookup(int kind, int store) {\n"
+             "  static const void* (*const table[4][5])() = {\n")
+    for kname, _ in KINDS:
+        fh.write("      {" + ", ".join(f"kernel_{kname}_{s}" for s, _ in STORES) + "},\n")
+    fh.write("  };\n  return table[kind][store]();\n}\n}  // namespace bs3\n")

@@ -1,0 +1,6 @@
+// Generated by gen_inst.py: solver kernel for circadian with f32 weights.
+#include "bs3_solver.cuh"
+
+namespace bs3 {
+const void* kernel_circadian_f32() { return (const void*)bs3_kernel<K_CIRCADIAN, ST_F32>; }
+}  // namespace bs3

@@ -1,0 +1,6 @@
+// Generated by gen_inst.py: solver kernel for lco_paper with bf16 weights.
+#include "bs3_solver.cuh"
+
+namespace bs3 {
+const void* kernel_lco_paper_bf16() { return (const void*)bs3_kernel<K_LCO_PAPER, ST_BF16>; }
+}  // namespace bs3

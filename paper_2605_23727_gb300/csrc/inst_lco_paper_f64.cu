@@ -1,0 +1,6 @@
+// Generated by gen_inst.py: solver kernel for lco_paper with f64 weights.
+#include "bs3_solver.cuh"
+
+namespace bs3 {
+const void* kernel_lco_paper_f64() { return (const void*)bs3_kernel<K_LCO_PAPER, ST_F64>; }
+}  // namespace bs3

@@ -50,6 +50,8 @@ def test_attempt_matches_oracle(kind, variant, accum):
     worst = max((rhs_tolerance(osys, X, obs3.VARIANTS[variant][s], accum) for s in (2, 3, 4)),
                 key=lambda v: v.sum())
     u = U32 if variant == "single" else U64
+    # a difference in one component reaches the others through the stage arguments
+    worst = np.full_like(worst, worst.max())
     tol_x = 2 * h * worst + 8 * u * (np.abs(Xn) + 1)
     assert np.all(np.abs(xn - Xn) <= tol_x)
     assert np.all(np.abs(k4 - K4) <= 4 * worst + 4 * u * (np.abs(K4) + 1))

@@ -58,12 +58,12 @@ def test_quantised_weights_bit_exact(store, N):
 @pytest.mark.parametrize("kind", models.KINDS)
 @pytest.mark.parametrize("store", STORES)
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("N", [37, 523])
-def test_rhs_matches_oracle(kind, store, prec, N):
+@pytest.mark.parametrize("N,resident", [(37, True), (523, True), (523, False)])
+def test_rhs_matches_oracle(kind, store, prec, N, resident):
     bs3 = library()
     torch = torch_cuda()
     w = _workload(kind, N)
-    sysm = bs3.System.from_workload(w, store)
+    sysm = bs3.System.from_workload(w, store, resident=resident)
     osys = models.from_workload(w, store)
     for accum in (ACCUMS if prec == ("D", "D", "S") else ["float2"]):
         got = _gpu_rhs(bs3, torch, sysm, w.y0, prec, accum)
@@ -90,7 +90,13 @@ def test_permutation_weights_give_exact_gather():
         sysm.set_coupling(P, store)
         got = _gpu_rhs(bs3, torch, sysm, y, ("D", "D", "D"), "float2")
         sysm.close()
-        np.testing.assert_array_equal(got[N:], y[:N][perm])
+        # one product per row: q_ij x_j is exact, then one rounding by the row scale
+        # (a power of two except for fp8, whose scale is fp32(1/448))
+        osys = models.make_system("lco_cfg", N, np.zeros(N), P, store)
+        ref = models.rhs(osys, 0.0, y, ("D", "D", "D"))
+        np.testing.assert_array_equal(got[N:], ref[N:])
+        if store != "fp8e4m3":
+            np.testing.assert_array_equal(got[N:], y[:N][perm])
 
 
 @pytest.mark.parametrize("kind,N,store", [("kuramoto", 4096, "bf16"), ("kuramoto", 4096, "f32"),

@@ -12,10 +12,10 @@ from tests.gpu_helpers import library, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _compare(w, store, variant, accum="float2", t_out=None, exact_y=None):
+def _compare(w, store, variant, accum="float2", t_out=None, exact_y=None, resident=True):
     bs3 = library()
     torch_cuda()
-    sysm = bs3.System.from_workload(w, store)
+    sysm = bs3.System.from_workload(w, store, resident=resident)
     rc, st, y, y_out = sysm.solve(w.t0, w.t1, w.y0, w.rtol, w.atol, variant, accum, t_out)
     sysm.close()
     osys = models.from_workload(w, store)
@@ -47,9 +47,10 @@ def test_lco_config_n256_all_variants(variant, accum):
 @pytest.mark.parametrize("variant,store", [("single", "f32"), ("mixed1", "f32"), ("mixed2", "f32"),
                                            ("double", "f64"), ("mixed1", "bf16"), ("mixed2", "f16"),
                                            ("mixed2", "fp8e4m3")])
-def test_kuramoto_small(variant, store):
+@pytest.mark.parametrize("resident", [True, False])
+def test_kuramoto_small(variant, store, resident):
     w = W.kuramoto(300, 2, t1=20.0)
-    st, y, _, ref, diff = _compare(w, store, variant)
+    st, y, _, ref, diff = _compare(w, store, variant, resident=resident)
     # both follow the same trajectory to well within the tolerance
     assert diff < 1e-3
 
@@ -73,10 +74,12 @@ def test_lco_paper_form_and_dense_output():
     np.testing.assert_allclose(y_out[-1], y, atol=0, rtol=0)
 
 
-def test_full_size_kuramoto_short_span():
-    """Config of the benchmark (N = 4096, bf16 weights, Mixed1) over t in [0, 1]."""
+@pytest.mark.parametrize("variant,store", [("mixed1", "bf16"), ("mixed1", "f32"), ("mixed2", "f32")])
+def test_full_size_kuramoto_short_span(variant, store):
+    """Benchmark workload (N = 4096) in the benchmark's launch configuration
+    (resident bf16 weights; streamed f32 weights) over t in [0, 1]."""
     w = W.kuramoto(4096, 0, t1=1.0)
-    _, _, _, _, diff = _compare(w, "bf16", "mixed1")
+    _, _, _, _, diff = _compare(w, store, variant)
     assert diff < 1e-6
 
 
