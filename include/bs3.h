@@ -192,6 +192,47 @@ int bs3_set_history(bs3_system_t sys, int64_t capacity);
  * binary64) and their number to *n_records. */
 int bs3_get_history(bs3_system_t sys, double* out, int64_t* n_records);
 
+/* Largest N accepted by bs3_solve_noalloc. */
+#define BS3_NOALLOC_MAX_N 16384
+
+/* bs3_solve without any device allocation, for callers that cannot allocate
+ * device memory at solve time: code that runs under an allocator or memory
+ * pool it does not own, a service with a fixed device-memory budget, or
+ * any setting where cudaMalloc is not allowed once start-up is over.  (A
+ * bs3 system allocates its buffers in bs3_create_system and bs3_set_coupling,
+ * so such callers cannot use bs3_solve.)  The paper has no counterpart.
+ *
+ * Scratch: one file-scope __device__ array of about 1.5 MB (j-vectors, row
+ * sums, row scales, k1/(k0-k1) and the control block for N <= 16384), which
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.
+ * All calls share the array and every call overwrites it, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Arguments (all arrays are device pointers of the current device unless noted):
+ *   kind, N       as bs3_create_system; 1 <= N <= BS3_NOALLOC_MAX_N;
+ *   par           N per-agent values (omega_i or k1_i; NULL for BS3_LCO_PAPER);
+ *   globals       host array of the 8 circadian constants k0, k2, k3, a, b, c,
+ *                 eps, I0 (NULL for the other kinds);
+ *   weights, store, ld
+ *                 the coupling weights already in their stored form: N rows of
+ *                 ld values of type store (BS3_F32 or BS3_F64, row scale 1),
+ *                 ld a multiple of 16 and >= N, columns N..ld-1 equal to zero,
+ *                 16-byte aligned;
+ *   the rest      as bs3_solve with device pointers (t_out ascending within
+ *                 [t0, t1]), stats on the host, stream a cudaStream_t or NULL.
+ * The failure limits are bs3_default_limits() except the wall-clock ones,
+ * which need host-mapped memory and are not enforced.  Returns the solve
+ * status after the results are complete; BS3_ERR_INVALID_ARG for N above
+ * BS3_NOALLOC_MAX_N or a malformed argument. */
+int bs3_solve_noalloc(int kind, int64_t N, const double* par, const double* globals,
+                      const void* weights, int store, int64_t ld, double t0, double t1,
+                      const double* y0, double rtol, double atol, int variant, int accum,
+                      const double* t_out, int64_t n_out, double* y_out, double* final_y,
+                      bs3_stats* stats, void* stream);
+
 /* Frees the system and everything it owns.  NULL is allowed. */
 int bs3_destroy_system(bs3_system_t sys);
 

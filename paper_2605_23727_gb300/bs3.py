@@ -35,8 +35,9 @@ STORE_NUMPY = {F64: np.float64, F32: np.float32, BF16: np.uint16, F16: np.float1
 EXPORTED = (
     "bs3_default_limits", "bs3_status_string", "bs3_create_system", "bs3_set_coupling",
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
-    "bs3_set_history", "bs3_get_history", "bs3_set_tuning",
+    "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
 )
+NOALLOC_MAX_N = 16384
 TUNE_RESIDENT_WEIGHTS = 1
 
 
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_destroy_system": (I, [P]),
         "bs3_set_history": (I, [P, I64]),
         "bs3_set_tuning": (I, [P, I, I64]),
+        "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
+                                  ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
@@ -178,6 +181,17 @@ def bs3_get_history(sys_: int, capacity: int):
     n = ctypes.c_int64()
     rc = load().bs3_get_history(sys_, _ptr(out), ctypes.byref(n))
     return rc, out[:n.value]
+
+
+def bs3_solve_noalloc(kind: int, N: int, par, globals_, weights, store: int, ld: int, t0: float, t1: float,
+                      y0, rtol: float, atol: float, variant: int, accum: int, t_out, n_out: int, y_out,
+                      final_y, stream: int = 0):
+    st = bs3_stats()
+    g = None if globals_ is None else np.ascontiguousarray(globals_, dtype=np.float64)
+    rc = load().bs3_solve_noalloc(kind, N, _ptr(par), _ptr(g), _ptr(weights), store, ld, t0, t1, _ptr(y0), rtol,
+                                  atol, variant, accum, _ptr(t_out), n_out, _ptr(y_out), _ptr(final_y),
+                                  ctypes.byref(st), stream or None)
+    return rc, st
 
 
 def bs3_destroy_system(sys_: int) -> int:
