@@ -49,6 +49,46 @@ CANDIDATES = [("double", "f64"), ("mixed2", "f32"), ("mixed1", "f32"), ("mixed2"
               ("mixed1", "bf16"), ("mixed1", "f16"), ("single", "f32")]
 
 
+# Single-solve cases for profiler captures (one persistent-kernel launch each):
+# name -> (workload builder, variant, stored weights)
+CASES = {
+    "kuramoto4096_mixed1_f32": (lambda: workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL), "mixed1", "f32"),
+    "kuramoto4096_mixed1_bf16": (lambda: workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL), "mixed1", "bf16"),
+    "kuramoto4096_double_f64": (lambda: workloads.kuramoto(4096, 0, t1=5.0, rtol=RTOL), "double", "f64"),
+    "lco16384_mixed1_f16": (lambda: workloads.lco_config(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "f16"),
+    "lco32768_mixed1_f16": (lambda: workloads.lco_config(32768, 0, t1=0.2, rtol=RTOL), "mixed1", "f16"),
+    "circadian16384_mixed1_bf16": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "bf16"),
+}
+
+
+def run_case(name):
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    make, variant, store = CASES[name]
+    w = make()
+    sysm = bs3.System.from_workload(w, store)
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(y0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rc, st = bs3.bs3_solve(sysm.handle, w.t0, w.t1, y0, w.rtol, w.atol, bs3.VARIANT_IDS[variant],
+                           bs3.ACC_FLOAT2, None, 0, None, y, 0)
+    e1.record()
+    e1.synchronize()
+    sysm.close()
+    print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "ms": e0.elapsed_time(e1),
+                      "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals,
+                      "N": w.N, "weights": store, "variant": variant,
+                      "weight_bytes_per_eval": w.N * w.N * STORE_BYTES[store]}))
+    if rc != bs3.OK:
+        sys.exit(1)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -57,7 +97,9 @@ def parse():
     ap.add_argument("--impl", default="bs3", choices=["bs3", "reference"])
     ap.add_argument("--accum", default="float2", choices=["float2", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-attempts", type=int, default=30)
+    ap.add_argument("--cpu-sample-attempts", type=int, default=150)
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="run one solve of a named case and print its stats (profiling runs)")
     return ap.parse_args()
 
 
@@ -66,6 +108,29 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def csrc_sha256():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2605_23727_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(case):
+    """DRAM bytes per launch from the committed ncu capture, or None once the
+    kernel sources have changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(case)
+    if not rec or rec.get("csrc_sha256") != csrc_sha256():
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
 def normalized_error(a, b, n):
@@ -284,9 +349,12 @@ def run_gpu(args):
                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + 64},
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None,
+                     "frac": round(achieved_gbs / hbm_peak, 4),
+                     "traffic": recorded_traffic(f"kuramoto4096_{h_variant}_{h_store}"),
                      "note": "algorithmic bytes = rhs_evals x (N^2 b_K + vectors) per solve launch; "
-                             "peak of measured (MEASURED_PEAKS.json hbm_gbs); weights are L2-resident at N=4096"},
+                             "peak of measured (MEASURED_PEAKS.json hbm_gbs); weights are L2-resident at N=4096, "
+                             "so DRAM traffic per launch (ncu) is far below the algorithmic bytes"},
+        "roofline_streaming": streaming_roofline(bs3, hbm_peak),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, h_variant, h_store, st.n_accepted + st.n_rejected,
@@ -297,6 +365,34 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(result))
+
+
+def streaming_roofline(bs3, hbm_peak):
+    """The coupling pass where the weights cannot stay on chip: second-order
+    oscillators, N = 16384, f16 weights (537 MB), Mixed1, t in [0, 0.5];
+    HBM bytes per solve = rhs_evals x N^2 x 2 B."""
+    import torch
+    make, variant, store = CASES["lco16384_mixed1_f16"]
+    w = make()
+    s = bs3.System.from_workload(w, store)
+    y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(y0)
+    best, st = None, None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, w.rtol, w.atol, bs3.VARIANT_IDS[variant],
+                               bs3.ACC_FLOAT2, None, 0, None, y, 0)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    s.close()
+    gbs = st.n_rhs_evals * w.N * w.N * STORE_BYTES[store] / (best * 1e-3) / 1e9
+    return {"bound": "hbm", "workload": "lco_cfg_N16384_f16_mixed1_t0.5", "achieved": round(gbs, 1),
+            "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+            "traffic": recorded_traffic("lco16384_mixed1_f16"), "ms": round(best, 3)}
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -352,7 +448,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.case:
+        run_case(a.case)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)
