@@ -192,6 +192,49 @@ int bs3_set_history(bs3_system_t sys, int64_t capacity);
  * binary64) and their number to *n_records. */
 int bs3_get_history(bs3_system_t sys, double* out, int64_t* n_records);
 
+/* ------------------------------------------------------------------------
+ * Learned step-size proposer (the paper has no learned component; this is the
+ * build's extension).  A small MLP, 6 -> 32 -> 32 -> 1 with tanh, proposes the
+ * next step size after an accepted step without rejections:
+ *   features [log r_{n-3}, log r_{n-2}, log r_{n-1}, log r_n, log h_n, log Rel],
+ *   r = clamp(E/Rel, 1e-8, 1e8) over the last accepted steps (missing ones
+ *   repeat the oldest), standardised by the model's mean and std;
+ *   h_{n+1} = h_n exp(clamp(out, log 0.2, log 5)).
+ * The embedded error test (Eq. ERROR-O23) still accepts or rejects every
+ * attempt, and a rejection falls back to the plain controller.
+ * A model is 1325 binary32: 1313 parameters (W1[32][6] row-major, b1[32],
+ * W2[32][32], b2[32], W3[32], b3) then mean[6], std[6].
+ * ------------------------------------------------------------------------ */
+#define BS3_MLP_PARAMS 1313
+#define BS3_MLP_MODEL 1325
+
+/* Training pairs from one solve's step history (bs3_get_history records):
+ * for consecutive accepted steps n, n+1, X[n] = features of step n (raw, not
+ * standardised; host, 6 binary32 each) and y[n] = log(h_star / h_n) with
+ * h_star = h_{n+1} (0.75 / r_{n+1})^(1/3), the step that would have given
+ * E = 0.75 Rel under E ~ h^3.  X and y need n_rec rows; *n_out receives the
+ * number written.  Host computation. */
+int bs3_mlp_dataset(const double* hist, int64_t n_rec, double rtol, float* X, float* y, int64_t* n_out);
+
+/* Trains the MLP on the GPU (per-sample forward/backward kernels, Adam with
+ * beta = (0.9, 0.999), eps 1e-8) on n raw samples (host X[n][6], y[n]),
+ * minimising 0.5 mean((out - y)^2) from params_init (host, 1313) for `epochs`
+ * shuffled passes of minibatches of `batch`.  Writes the model (host, 1325:
+ * parameters, then the inputs' mean and std) and, if loss_hist is not NULL,
+ * each epoch's mean minibatch loss. */
+int bs3_mlp_train(const float* X, const float* y, int64_t n, const float* params_init, int epochs, int batch,
+                  float lr, uint64_t seed, float* model_out, float* loss_hist);
+
+/* Loss 0.5 mean((out - y)^2) and its gradient (host, 1313) at params (host,
+ * 1313) over n standardised samples (host), computed by the training kernel. */
+int bs3_mlp_grad(const float* params, const float* X, const float* y, int64_t n, float* grad_out,
+                 float* loss_out);
+
+/* Installs a trained model (host, 1325 binary32; weights rounded to bfloat16
+ * for inference) in the system, or removes it (model = NULL).  Errors:
+ * BS3_ERR_INVALID_ARG for non-finite values or a non-positive std. */
+int bs3_set_proposer(bs3_system_t sys, const float* model);
+
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384
 

@@ -36,7 +36,10 @@ EXPORTED = (
     "bs3_default_limits", "bs3_status_string", "bs3_create_system", "bs3_set_coupling",
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
+    "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer",
 )
+MLP_PARAMS = 1313
+MLP_MODEL = 1325
 NOALLOC_MAX_N = 16384
 TUNE_RESIDENT_WEIGHTS = 1
 
@@ -91,6 +94,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_destroy_system": (I, [P]),
         "bs3_set_history": (I, [P, I64]),
         "bs3_set_tuning": (I, [P, I, I64]),
+        "bs3_mlp_dataset": (I, [P, I64, D, P, P, ctypes.POINTER(I64)]),
+        "bs3_mlp_train": (I, [P, P, I64, P, I, I, ctypes.c_float, ctypes.c_uint64, P, P]),
+        "bs3_mlp_grad": (I, [P, P, P, I64, P, P]),
+        "bs3_set_proposer": (I, [P, P]),
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
@@ -192,6 +199,45 @@ def bs3_solve_noalloc(kind: int, N: int, par, globals_, weights, store: int, ld:
                                   atol, variant, accum, _ptr(t_out), n_out, _ptr(y_out), _ptr(final_y),
                                   ctypes.byref(st), stream or None)
     return rc, st
+
+
+def bs3_mlp_dataset(hist, rtol: float):
+    """Returns (rc, X[n, 6] float32, y[n] float32) from history records [n_rec, 8]."""
+    hist = np.ascontiguousarray(hist, dtype=np.float64)
+    n_rec = hist.shape[0]
+    X = np.zeros((max(n_rec, 1), 6), dtype=np.float32)
+    y = np.zeros(max(n_rec, 1), dtype=np.float32)
+    n = ctypes.c_int64()
+    rc = load().bs3_mlp_dataset(_ptr(hist), n_rec, rtol, _ptr(X), _ptr(y), ctypes.byref(n))
+    return rc, X[:n.value], y[:n.value]
+
+
+def bs3_mlp_train(X, y, params_init, epochs: int, batch: int, lr: float, seed: int):
+    """Returns (rc, model[1325] float32, loss_hist[epochs] float32)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    p0 = np.ascontiguousarray(params_init, dtype=np.float32)
+    model = np.zeros(MLP_MODEL, dtype=np.float32)
+    hist = np.zeros(epochs, dtype=np.float32)
+    rc = load().bs3_mlp_train(_ptr(X), _ptr(y), X.shape[0], _ptr(p0), epochs, batch, lr, seed, _ptr(model),
+                              _ptr(hist))
+    return rc, model, hist
+
+
+def bs3_mlp_grad(params, X, y):
+    """Returns (rc, loss, grad[1313] float32)."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    rc = load().bs3_mlp_grad(_ptr(p), _ptr(X), _ptr(y), X.shape[0], _ptr(g), ctypes.byref(loss))
+    return rc, loss.value, g
+
+
+def bs3_set_proposer(sys_: int, model) -> int:
+    m = None if model is None else np.ascontiguousarray(model, dtype=np.float32)
+    return load().bs3_set_proposer(sys_, _ptr(m))
 
 
 def bs3_destroy_system(sys_: int) -> int:

@@ -18,6 +18,7 @@
 #include "../../include/bs3.h"
 #include "bs3_device.cuh"
 #include "bs3_kernels.h"
+#include "bs3_mlp.cuh"
 #include "bs3_solver.cuh"
 
 using namespace bs3;
@@ -61,6 +62,9 @@ struct bs3_system {
   size_t smem = 0;
   int slab = 0;
   bool allow_resident = true;
+  float* mlp = nullptr;        // learned proposer (kMlpModel binary32, weights bf16-rounded)
+  bool mlp_on = false;
+  int mlp_off = 0;
   int grid_store = -1;
 };
 
@@ -218,14 +222,16 @@ int pick_grid(bs3_system* s) {
   const int rb = rows_per_tile(s->kind);
   const int64_t grid = std::min<int64_t>(sms, std::max<int64_t>(1, (s->N + rb - 1) / rb));
   const int rc = (int)((s->N + grid - 1) / grid);
-  const size_t state = state_smem_bytes(s->d, rc);
-  if (state > (size_t)200 * 1024) return BS3_ERR_INVALID_ARG;
+  const size_t state = (state_smem_bytes(s->d, rc) + 15) / 16 * 16;
+  const size_t mlp = s->mlp_on ? (size_t)kMlpModel * sizeof(float) : 0;
+  if (state + mlp > (size_t)200 * 1024) return BS3_ERR_INVALID_ARG;
   // keep each CTA's weight rows resident in shared memory when they fit
   // (streaming kinds only; the pairwise arctangent kernel is ALU-bound)
   const size_t slab = ((size_t)rc * s->ld * store_bytes(s->store) + 127) / 128 * 128;
   const size_t budget = (size_t)224 * 1024;
-  const bool resident = s->kind != BS3_CIRCADIAN && s->allow_resident && slab + state <= budget;
-  const size_t smem = (resident ? slab : 0) + state;
+  const bool resident = s->kind != BS3_CIRCADIAN && s->allow_resident && slab + state + mlp <= budget;
+  const size_t smem = (resident ? slab : 0) + state + mlp;
+  s->mlp_off = (int)((resident ? slab : 0) + state);
   BS3_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int nb = 0;
   BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem));
@@ -268,6 +274,8 @@ int launch(bs3_system* s, Args& a) {
   if (rc != BS3_OK) return rc;
   a.rc = s->rc;
   a.slab_bytes = s->slab;
+  a.mlp = s->mlp_on ? s->mlp : nullptr;
+  a.smem_mlp_off = s->mlp_off;
   BS3_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(Control), s->stream));
   void* params[] = {&a};
   BS3_CUDA(cudaLaunchCooperativeKernel(kernel_for(s->kind, s->store), dim3(s->grid), dim3(kBlock), params,
@@ -387,6 +395,34 @@ int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_param
   return BS3_OK;
 }
 
+int bs3_set_proposer(bs3_system_t s, const float* model) {
+  if (!s) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  s->grid_store = -1;   // the shared-memory plan changes
+  if (!model) {
+    s->mlp_on = false;
+    return BS3_OK;
+  }
+  float h[kMlpModel];
+  for (int k = 0; k < kMlpModel; ++k) {
+    if (!std::isfinite(model[k])) return BS3_ERR_INVALID_ARG;
+    h[k] = model[k];
+  }
+  for (int k = kMlpModel - kMlpIn; k < kMlpModel; ++k)
+    if (!(h[k] > 0.f)) return BS3_ERR_INVALID_ARG;   // standard deviations
+  // inference weights in bfloat16 (round to nearest even), kept as binary32
+  for (int k = 0; k < kMlpParams; ++k) {
+    uint32_t u;
+    std::memcpy(&u, &h[k], 4);
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    std::memcpy(&h[k], &u, 4);
+  }
+  if (!s->mlp) BS3_CUDA(cudaMalloc(&s->mlp, kMlpModel * sizeof(float)));
+  BS3_CUDA(cudaMemcpy(s->mlp, h, kMlpModel * sizeof(float), cudaMemcpyHostToDevice));
+  s->mlp_on = true;
+  return BS3_OK;
+}
+
 int bs3_set_tuning(bs3_system_t s, int key, int64_t value) {
   if (!s) return BS3_ERR_INVALID_ARG;
   if (key == BS3_TUNE_RESIDENT_WEIGHTS) {
@@ -439,6 +475,7 @@ int bs3_destroy_system(bs3_system_t s) {
   cudaFree(s->stage_in);
   cudaFree(s->stage_out);
   cudaFree(s->hist);
+  cudaFree(s->mlp);
   if (s->cancel_h) cudaFreeHost(s->cancel_h);
   if (s->progress_h) cudaFreeHost(s->progress_h);
   delete s;

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "bs3_device.cuh"
+#include "bs3_mlp.cuh"
 
 namespace bs3 {
 
@@ -52,6 +53,8 @@ struct Args {
   int slab_bytes;           // > 0: each CTA keeps its rc weight rows in shared memory
   double* hist;             // optional per-attempt records [hist_cap][kHistDoubles]
   long long hist_cap;
+  const float* mlp;         // optional learned proposer: kMlpModel binary32 (bf16-rounded weights)
+  int smem_mlp_off;         // byte offset of its shared-memory copy in the dynamic region
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -595,6 +598,9 @@ struct Scal {
   double t, h, hs, c21, c32, E, hstep, tstep0;
   long long n_acc, n_rej, n_rhs, next_out, out_end;
   int status, last, stop, accepted, rejected, parity;
+  int mlp_go, n_ehist;
+  double ehist[4];          // errors of the last accepted steps (learned proposer)
+  float feat[kMlpIn];
   double theta[kThetaMax];
 };
 
@@ -639,6 +645,9 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     const int n16 = (int)((size_t)x.nr * a.ld * eb / 16);
     for (int e = tid; e < n16; e += blockDim.x) dst[e] = ld_stream16(src + e);
   }
+  float* smlp = a.mlp ? (float*)(dyn + a.smem_mlp_off) : nullptr;
+  if (a.mlp)
+    for (int k = tid; k < kMlpModel; k += blockDim.x) smlp[k] = a.mlp[k];
   // per-agent parameters and the initial state of this CTA's agents
   for (int li = tid; li < x.nr; li += blockDim.x) {
     const int i = x.rb + li;
@@ -683,6 +692,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     sc.t = a.t0; sc.h = a.h_given; sc.E = 0.0;
     sc.n_acc = 0; sc.n_rej = 0; sc.n_rhs = 0; sc.next_out = 0; sc.out_end = 0;
     sc.status = S_OK; sc.last = 0; sc.stop = 0; sc.accepted = 0; sc.rejected = 0; sc.parity = 0;
+    sc.mlp_go = 0; sc.n_ehist = 0;
     if (a.job == JOB_SOLVE)
       while (sc.next_out < a.n_out && a.t_out[sc.next_out] <= a.t0) ++sc.next_out;
   }
@@ -807,7 +817,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
     block_max(x.m1, &ctrl->emax[parity], s_red);
     if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
-    // ---- decision (thread 0)
+    // ---- decision (thread 0; warp 0 runs the learned proposer when installed)
     if (tid == 0) {
       const double E = ld_bits(&ctrl->emax[parity]);
       sc.E = E;
@@ -840,14 +850,36 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
         sc.h = h * fac;
         sc.t = t_new;
         ++sc.n_acc;
+        if (sc.n_ehist == 4) {
+          for (int k = 0; k < 3; ++k) sc.ehist[k] = sc.ehist[k + 1];
+          sc.ehist[3] = E;
+        } else {
+          sc.ehist[sc.n_ehist++] = E;
+        }
+        sc.mlp_go = (smlp != nullptr) && !sc.rejected;
+        if (sc.mlp_go) {
+          double f[kMlpIn];
+          mlp_features(sc.ehist, sc.n_ehist, h, rtol, f);
+          for (int k = 0; k < kMlpIn; ++k)
+            sc.feat[k] = ((float)f[k] - smlp[kMlpParams + k]) / smlp[kMlpParams + kMlpIn + k];
+        }
         sc.rejected = 0;
         sc.accepted = 1;
       } else {
         ++sc.n_rej;
         sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * pow(rtol / E, 1.0 / 3.0));
         sc.rejected = 1;
+        sc.mlp_go = 0;
       }
       sc.parity ^= 1;
+    }
+    if (smlp != nullptr && tid < 32) {
+      __syncwarp();
+      if (sc.accepted && sc.mlp_go) {
+        // learned proposal of the next step (the error test still decides)
+        const float dlt = mlp_warp_forward(smlp, sc.feat, tid);
+        if (tid == 0) sc.h = sc.hstep * exp(fmin(fmax((double)dlt, kMlpDMin), kMlpDMax));
+      }
     }
     __syncthreads();
     if (a.job == JOB_ATTEMPT) {
