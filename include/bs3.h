@@ -168,9 +168,11 @@ int bs3_solve(bs3_system_t sys, double t0, double t1, const double* y0, double r
 
 /* Tuning knobs (bs3_set_tuning keys). */
 enum {
-    /* 1 (default): when the weight rows of every CTA fit in its shared memory
-     * (one CTA per SM), load them once per solve and keep them on chip; 0:
-     * always stream them from HBM/L2 at every stage.  Results are identical. */
+    /* 1: when the weight rows of every CTA fit in its shared memory (one CTA
+     * per SM), load them once per solve and keep them on chip; 0 (default):
+     * stream them from HBM/L2 at every stage.  Results are identical.  On
+     * GB300 keeping them on chip leaves too little L1 for the j-vectors and
+     * measured slower (Kuramoto N=4096, bf16: 64.5 vs 61.7 ms). */
     BS3_TUNE_RESIDENT_WEIGHTS = 1
 };
 

@@ -263,11 +263,11 @@ class System:
 
     @classmethod
     def from_workload(cls, w, store: str = "f64", device: int = 0, stream: int = 0,
-                      resident: bool = True) -> "System":
+                      resident: bool = False) -> "System":
         s = cls(w.kind, w.N, w.params, w.globals, device, stream)
         s.set_coupling(w.coupling, store)
-        if not resident:
-            rc = bs3_set_tuning(s.handle, TUNE_RESIDENT_WEIGHTS, 0)
+        if resident:
+            rc = bs3_set_tuning(s.handle, TUNE_RESIDENT_WEIGHTS, 1)
             if rc != OK:
                 raise RuntimeError(bs3_status_string(rc))
         return s

@@ -61,7 +61,8 @@ struct bs3_system {
   int rc = 0;
   size_t smem = 0;
   int slab = 0;
-  bool allow_resident = true;
+  bool allow_resident = false;   // see BS3_TUNE_RESIDENT_WEIGHTS
+  int l2_keep = 1;
   float* mlp = nullptr;        // learned proposer (kMlpModel binary32, weights bf16-rounded)
   bool mlp_on = false;
   int mlp_off = 0;
@@ -236,6 +237,9 @@ int pick_grid(bs3_system* s) {
   int nb = 0;
   BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem));
   if (nb < 1) return BS3_ERR_CUDA;
+  int l2 = 0;
+  BS3_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, s->device));
+  s->l2_keep = ((double)s->N * s->ld * store_bytes(s->store) <= 0.6 * (double)l2) ? 1 : 0;
   s->grid = (int)grid;
   s->rc = rc;
   s->smem = smem;
@@ -276,6 +280,7 @@ int launch(bs3_system* s, Args& a) {
   a.slab_bytes = s->slab;
   a.mlp = s->mlp_on ? s->mlp : nullptr;
   a.smem_mlp_off = s->mlp_off;
+  a.l2_keep = s->l2_keep;
   BS3_CUDA(cudaMemsetAsync(s->ctrl, 0, sizeof(Control), s->stream));
   void* params[] = {&a};
   BS3_CUDA(cudaLaunchCooperativeKernel(kernel_for(s->kind, s->store), dim3(s->grid), dim3(kBlock), params,

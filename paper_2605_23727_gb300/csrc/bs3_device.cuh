@@ -70,6 +70,24 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   return r;
 }
 
+// 16-byte weight load with an L2 eviction-priority policy (createpolicy):
+// evict_last keeps weights that fit in L2 resident across stages even after
+// other traffic, evict_first keeps a weight stream larger than L2 from
+// evicting the j-vectors.
+__device__ __forceinline__ unsigned long long l2_policy(bool keep) {
+  unsigned long long pol;
+  if (keep) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  else asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint4 ld_stream16_pol(const void* p, unsigned long long pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p), "l"(pol));
+  return r;
+}
+
 // Grid barrier for a cooperative launch.  Every CTA adds one arrival to a
 // monotonic counter (release) and polls it until it reaches its target.  The
 // wait is bounded by spin_limit polls; a CTA that gives up sets the status to

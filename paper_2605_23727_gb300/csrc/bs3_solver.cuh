@@ -51,6 +51,7 @@ struct Args {
   long long max_attempts, max_rejects, spin_limit;
   int rc;                   // rows per CTA capacity (ceil(N / grid))
   int slab_bytes;           // > 0: each CTA keeps its rc weight rows in shared memory
+  int l2_keep;              // 1: weights fit in L2, load them evict_last; 0: evict_first
   double* hist;             // optional per-attempt records [hist_cap][kHistDoubles]
   long long hist_cap;
   const float* mlp;         // optional learned proposer: kMlpModel binary32 (bf16-rounded weights)
@@ -130,8 +131,11 @@ __device__ __forceinline__ void merge(Acc<M_SD2>& x, unsigned long long b) {
   x.lo = __fadd_rn(__fadd_rn(x.lo, olo), e);
 }
 
-__device__ __forceinline__ void group_bar(int g) {
-  asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(kGroupThreads) : "memory");
+// Synchronises the gt threads of warp group g (a single warp needs only a
+// warp barrier; larger groups use named barrier 1 + g).
+__device__ __forceinline__ void group_bar(int g, int gt) {
+  if (gt == 32) __syncwarp();
+  else asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(gt) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -139,7 +143,7 @@ __device__ __forceinline__ void group_bar(int g) {
 // columns of thread lt of a 128-thread group; then a warp-level reduction.
 // ---------------------------------------------------------------------------
 template <int ST, int MODE, int NV, int RB, bool RES>
-__device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int lrow0, int nrows, int lt,
+__device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int lrow0, int nrows, int lt, int gt,
                                          const unsigned char* slab, Acc<MODE> (&acc)[RB][NV]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
@@ -150,13 +154,15 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
   const size_t rstride = (size_t)a.ld * L::BYTES;
   const float* v32 = a.jv32 + (size_t)(buf * 2) * a.ld;
   const double* v64 = a.jv64 + (size_t)(buf * 2) * a.ld;
+  const unsigned long long pol = l2_policy(a.l2_keep != 0);
 #pragma unroll(VEC >= 16 ? 1 : 2)
-  for (int col = lt * VEC; col < a.ld; col += kGroupThreads * VEC) {
+  for (int col = lt * VEC; col < a.ld; col += gt * VEC) {
     uint4 raw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const char* p = qb + (size_t)r * rstride + (size_t)col * L::BYTES;
-      raw[r] = (r < nrows) ? (RES ? *reinterpret_cast<const uint4*>(p) : ld_stream16(p)) : make_uint4(0u, 0u, 0u, 0u);
+      raw[r] = (r < nrows) ? (RES ? *reinterpret_cast<const uint4*>(p) : ld_stream16_pol(p, pol))
+                           : make_uint4(0u, 0u, 0u, 0u);
     }
     if (!DD) {
       float vv[NV][VEC];
@@ -213,7 +219,7 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
 
 // Circadian interaction: r_i = sum_j q_ij atan(x_j - x_i) (Eq. CC).
 template <int ST, int MODE, int RB>
-__device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nrows, int lt,
+__device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nrows, int lt, int gt,
                                        Acc<MODE> (&acc)[RB][1]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
@@ -222,6 +228,7 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
   const size_t rstride = (size_t)a.ld * L::BYTES;
   const float* v32 = a.jv32 + (size_t)(buf * 2) * a.ld;
   const double* v64 = a.jv64 + (size_t)(buf * 2) * a.ld;
+  const unsigned long long pol = l2_policy(a.l2_keep != 0);
   float xi32[RB];
   double xi64[RB];
 #pragma unroll
@@ -230,11 +237,11 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
     xi32[r] = DD ? 0.f : v32[i];
     xi64[r] = DD ? v64[i] : 0.0;
   }
-  for (int col = lt * VEC; col < a.ld; col += kGroupThreads * VEC) {
+  for (int col = lt * VEC; col < a.ld; col += gt * VEC) {
     uint4 raw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
-      raw[r] = (r < nrows) ? ld_stream16(qb + (size_t)(row0 + r) * rstride + (size_t)col * L::BYTES)
+      raw[r] = (r < nrows) ? ld_stream16_pol(qb + (size_t)(row0 + r) * rstride + (size_t)col * L::BYTES, pol)
                            : make_uint4(0u, 0u, 0u, 0u);
     if (!DD) {
       float xj[VEC];
@@ -380,6 +387,7 @@ enum Phase { PH_RHS = 0, PH_K1 = 1, PH_F1 = 2, PH_B2 = 3, PH_B3 = 4, PH_B4 = 5 }
 
 struct Ctx {
   const unsigned char* slab;  // shared-memory copy of this CTA's weight rows (or null)
+  int gt;                     // threads per warp group of the coupling pass
   double* S;          // shared state slots
   double* spar;       // shared per-agent omega_i / k1_i
   double* sth;        // shared k1/(k0-k1)
@@ -506,56 +514,59 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int l
 // warp groups; each group reduces its partial sums through shared memory
 // and the first RB threads of the group run the epilogues.
 // ---------------------------------------------------------------------------
-template <int KIND, int ST, int MODE, bool RES>
+template <int KIND, int ST, int MODE, bool RES, int RB>
 __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
-  constexpr int RB = rows_per_tile(KIND);
   constexpr int NV = (KIND == K_KURAMOTO) ? 2 : 1;
-  const int g = threadIdx.x / kGroupThreads, lt = threadIdx.x % kGroupThreads;
+  // warp groups of gt threads (4 x 128, 8 x 64 or 16 x 32) each take RB rows at
+  // a time; the smallest groups that still cover the CTA's rows in one pass
+  const int gt = x.gt, ng = kBlock / gt, wpg = gt >> 5;
+  const int g = threadIdx.x / gt, lt = threadIdx.x % gt;
   const int wig = lt >> 5, lane = lt & 31;
   const int nrb = (x.nr + RB - 1) / RB;
-  for (int rbk = g; rbk < nrb; rbk += kGroups) {
+  for (int rbk = g; rbk < nrb; rbk += ng) {
     const int lrow0 = rbk * RB;
     const int nrows = min(RB, x.nr - lrow0);
     Acc<MODE> acc[RB][NV];
-    if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, (Acc<MODE>(&)[RB][1])acc);
-    else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, x.slab, acc);
+    if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, gt, (Acc<MODE>(&)[RB][1])acc);
+    else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, gt, x.slab, acc);
+    const int wbase = g * wpg;   // first warp of this group
     if (lane == 0) {
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int n = 0; n < NV; ++n) red[((g * 4 + wig) * kRBMax + r) * 2 + n] = pack(acc[r][n]);
+        for (int n = 0; n < NV; ++n) red[((wbase + wig) * kRBMax + r) * 2 + n] = pack(acc[r][n]);
     }
-    group_bar(g);
+    group_bar(g, gt);
     if (lt < nrows) {
       double s[2] = {0.0, 0.0};
 #pragma unroll
       for (int n = 0; n < NV; ++n) {
         Acc<MODE> tot;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) merge(tot, red[((g * 4 + w) * kRBMax + lt) * 2 + n]);
+        for (int w = 0; w < wpg; ++w) merge(tot, red[((wbase + w) * kRBMax + lt) * 2 + n]);
         s[n] = tot.value();
       }
       epilogue<KIND>(a, x, phase, lrow0 + lt, s[0], s[1]);
     }
-    group_bar(g);
+    group_bar(g, gt);
   }
 }
 
-template <int KIND, int ST, bool RES>
+template <int KIND, int ST, bool RES, int RB>
 __device__ __forceinline__ void stage_r(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
   switch (sum_mode(x.p, a.accum)) {
-    case M_SS: stage_m<KIND, ST, M_SS, RES>(a, x, phase, buf, red); break;
-    case M_SD64: stage_m<KIND, ST, M_SD64, RES>(a, x, phase, buf, red); break;
-    case M_SD2: stage_m<KIND, ST, M_SD2, RES>(a, x, phase, buf, red); break;
-    default: stage_m<KIND, ST, M_DD, RES>(a, x, phase, buf, red); break;
+    case M_SS: stage_m<KIND, ST, M_SS, RES, RB>(a, x, phase, buf, red); break;
+    case M_SD64: stage_m<KIND, ST, M_SD64, RES, RB>(a, x, phase, buf, red); break;
+    case M_SD2: stage_m<KIND, ST, M_SD2, RES, RB>(a, x, phase, buf, red); break;
+    default: stage_m<KIND, ST, M_DD, RES, RB>(a, x, phase, buf, red); break;
   }
 }
 
 // The circadian interaction is ALU-bound and always streams its weights.
 template <int KIND, int ST>
 __device__ __forceinline__ void stage(const Args& a, Ctx& x, int phase, int buf, unsigned long long* red) {
-  if (KIND != K_CIRCADIAN && x.slab != nullptr) stage_r<KIND, ST, (KIND != K_CIRCADIAN)>(a, x, phase, buf, red);
-  else stage_r<KIND, ST, false>(a, x, phase, buf, red);
+  constexpr int RB = rows_per_tile(KIND);
+  if (KIND != K_CIRCADIAN && x.slab != nullptr) stage_r<KIND, ST, (KIND != K_CIRCADIAN), RB>(a, x, phase, buf, red);
+  else stage_r<KIND, ST, false, RB>(a, x, phase, buf, red);
 }
 
 // Block-wide max of non-negative binary64 values (bit patterns), then one
@@ -610,7 +621,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ int s_abort;
   __shared__ unsigned long long s_red[kBlock / 32];
-  __shared__ unsigned long long s_grp[kGroups * 4 * kRBMax * 2];
+  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
   __shared__ Scal sc;
   const int N = a.N;
   const int G = gridDim.x, b = blockIdx.x;
@@ -621,6 +632,13 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
 
   Ctx x;
   x.rc = a.rc;
+  {
+    // smallest warp groups (>= 32 threads) whose row blocks cover rc rows in one pass
+    constexpr int RBk = rows_per_tile(KIND);
+    int gt = kBlock / 4;
+    while (gt > 32 && (kBlock / gt) * RBk < a.rc) gt >>= 1;
+    x.gt = gt;
+  }
   x.rb = (int)(((long long)b * N) / G);
   x.nr = (int)(((long long)(b + 1) * N) / G) - x.rb;
   x.slab = a.slab_bytes > 0 ? dyn : nullptr;

@@ -58,7 +58,7 @@ def test_quantised_weights_bit_exact(store, N):
 @pytest.mark.parametrize("kind", models.KINDS)
 @pytest.mark.parametrize("store", STORES)
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("N,resident", [(37, True), (523, True), (523, False)])
+@pytest.mark.parametrize("N,resident", [(37, False), (37, True), (523, True), (523, False)])
 def test_rhs_matches_oracle(kind, store, prec, N, resident):
     bs3 = library()
     torch = torch_cuda()

@@ -12,7 +12,7 @@ from tests.gpu_helpers import library, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _compare(w, store, variant, accum="float2", t_out=None, exact_y=None, resident=True):
+def _compare(w, store, variant, accum="float2", t_out=None, exact_y=None, resident=False):
     bs3 = library()
     torch_cuda()
     sysm = bs3.System.from_workload(w, store, resident=resident)
