@@ -237,6 +237,16 @@ int bs3_mlp_grad(const float* params, const float* X, const float* y, int64_t n,
  * BS3_ERR_INVALID_ARG for non-finite values or a non-positive std. */
 int bs3_set_proposer(bs3_system_t sys, const float* model);
 
+/* Tensor-core product used by ensembles that share one coupling matrix
+ * (the build's extension; the paper has no batching):
+ *   C = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,
+ * A (M x K) and B (Nc x K) binary32 row-major, split into bfloat16 pairs
+ * x_hi = bf16(x), x_lo = bf16(x - x_hi) (nearest even), products accumulated
+ * in binary32 by tcgen05.mma in tensor memory; C (M x Nc) binary32 row-major.
+ * All device pointers.  Requires M % 128 == 0, Nc % 256 == 0, K % 64 == 0.
+ * Returns BS3_ERR_DEVICE_WAIT if a bounded pipeline wait ran out. */
+int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C);
+
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384
 

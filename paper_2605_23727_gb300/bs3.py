@@ -36,7 +36,7 @@ EXPORTED = (
     "bs3_default_limits", "bs3_status_string", "bs3_create_system", "bs3_set_coupling",
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
-    "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer",
+    "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
 )
 MLP_PARAMS = 1313
 MLP_MODEL = 1325
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_mlp_train": (I, [P, P, I64, P, I, I, ctypes.c_float, ctypes.c_uint64, P, P]),
         "bs3_mlp_grad": (I, [P, P, P, I64, P, P]),
         "bs3_set_proposer": (I, [P, P]),
+        "bs3_tc_gemm": (I, [I64, I64, I64, P, P, P]),
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
@@ -238,6 +239,10 @@ def bs3_mlp_grad(params, X, y):
 def bs3_set_proposer(sys_: int, model) -> int:
     m = None if model is None else np.ascontiguousarray(model, dtype=np.float32)
     return load().bs3_set_proposer(sys_, _ptr(m))
+
+
+def bs3_tc_gemm(M: int, Nc: int, K: int, A, B, C) -> int:
+    return load().bs3_tc_gemm(M, Nc, K, _ptr(A), _ptr(B), _ptr(C))
 
 
 def bs3_destroy_system(sys_: int) -> int:
