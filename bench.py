@@ -59,10 +59,45 @@ CASES = {
     "lco16384_mixed1_f16": (lambda: workloads.lco_config(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "f16"),
     "lco32768_mixed1_f16": (lambda: workloads.lco_config(32768, 0, t1=0.2, rtol=RTOL), "mixed1", "f16"),
     "circadian16384_mixed1_bf16": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "bf16"),
+    "ensemble256_kuramoto8192": None,
+    "ensemble128_kuramoto1024": None,
 }
 
 
+def run_ensemble_case(name):
+    """Shared-K ensemble on the tensor cores: T Kuramoto trajectories, one K."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    T, N, t1 = {"ensemble256_kuramoto8192": (256, 8192, T1), "ensemble128_kuramoto1024": (128, 1024, 10.0)}[name]
+    K, omega, theta0 = workloads.kuramoto_ensemble(T=T, N=N, seed=0)
+    Kd = torch.tensor(K, dtype=torch.float32, device="cuda")
+    om = torch.tensor(omega, dtype=torch.float64, device="cuda")
+    th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(th)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rc, n_acc, n_rej, status, steps = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, RTOL, RTOL, out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    flops = 3 * 3 * 2.0 * N * N * (2 * T) * steps     # 3 stages x 3 split products per lock-step attempt
+    print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "ms": ms, "T": T, "N": N,
+                      "lockstep_attempts": steps, "attempts_max": int((n_acc + n_rej).max()),
+                      "attempts_mean": float((n_acc + n_rej).mean()), "all_ok": bool((status == 0).all()),
+                      "tensor_tflops": flops / (ms * 1e-3) / 1e12,
+                      "ms_per_trajectory": ms / T}))
+    if rc != bs3.OK:
+        sys.exit(1)
+
+
 def run_case(name):
+    if name.startswith("ensemble"):
+        return run_ensemble_case(name)
     import torch
     from paper_2605_23727_gb300 import bs3
     import __graft_entry__

@@ -247,6 +247,24 @@ int bs3_set_proposer(bs3_system_t sys, const float* model);
  * Returns BS3_ERR_DEVICE_WAIT if a bounded pipeline wait ran out. */
 int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C);
 
+/* Lock-step ensemble of T Kuramoto trajectories sharing one coupling matrix
+ * (the build's batched extension): theta_b' = omega_b + sum_j K_ij sin(theta_bj
+ * - theta_bi), b = 0..T-1, each trajectory with its own adaptive h, t and
+ * accept/reject decision (the controller and failure conditions of bs3_solve),
+ * all stages of all live trajectories computed together on the tensor cores:
+ * G = bfloat16 hi+lo split of K and of sin/cos (bs3_tc_gemm's three products),
+ * Sigma = binary32 accumulation and i-side finish, F and the state, stage
+ * combinations and error norm in binary64 (the oracle's "tensor" variant).
+ * K: device, N x N binary32 row-major; omega, theta0, theta_out: device,
+ * [T][N] binary64 (trajectory-major).  N % 128 == 0, T % 128 == 0.
+ * n_acc, n_rej, status (host arrays of T, may be NULL) receive each
+ * trajectory's counts and status; *lockstep_attempts (host, may be NULL) the
+ * number of lock-step attempts run.  Waits for completion.  Returns
+ * BS3_ERR_DEVICE_WAIT if a bounded pipeline wait ran out. */
+int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                       double t0, double t1, double rtol, double atol, double* theta_out, int64_t* n_acc,
+                       int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream);
+
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384
 

@@ -73,7 +73,11 @@ VARIANTS = {
     "mixed1": {2: ("S", "S", "S"), 3: ("S", "S", "S"), 4: ("D", "D", "S")},
     "mixed2": {2: ("D", "D", "S"), 3: ("D", "D", "S"), 4: ("D", "D", "S")},
     "double": {2: ("D", "D", "D"), 3: ("D", "D", "D"), 4: ("D", "D", "D")},
+    # ensembles sharing K on the tensor cores (models.rhs_tensor), state in binary64
+    "tensor": {2: "T", 3: "T", 4: "T"},
 }
+
+PAPER_VARIANTS = ("single", "mixed1", "mixed2", "double")
 
 C = as_float(BS3_C)
 A = as_float(BS3_A)
@@ -126,6 +130,10 @@ def error_norm(X, Xn, Dv, rtol, atol):
     return float(np.max(np.abs(Dv.astype(np.float64)) / W)) if X.size else 0.0
 
 
+def _rhs(sysm, t, y, prec):
+    return models.rhs_tensor(sysm, t, y) if prec == "T" else models.rhs(sysm, t, y, prec)
+
+
 def attempt(sysm, t, X, K1, h, variant, rtol, atol):
     """One BS3 attempt: returns (Xn, K4, E, (K2, K3)).  State dtype decides the
     precision of the stage combinations (binary32 for Single)."""
@@ -134,11 +142,11 @@ def attempt(sysm, t, X, K1, h, variant, rtol, atol):
     hs = st(h)
     # the scalar a_lm h is formed in the state precision
     Y2 = X + (st(A[1][0]) * hs) * K1
-    K2 = models.rhs(sysm, t + C[1] * h, Y2, prec[2])
+    K2 = _rhs(sysm, t + C[1] * h, Y2, prec[2])
     Y3 = X + (st(A[2][1]) * hs) * K2
-    K3 = models.rhs(sysm, t + C[2] * h, Y3, prec[3])
+    K3 = _rhs(sysm, t + C[2] * h, Y3, prec[3])
     Xn = X + hs * (st(B[0]) * K1 + st(B[1]) * K2 + st(B[2]) * K3)
-    K4 = models.rhs(sysm, t + h, Xn, prec[4])
+    K4 = _rhs(sysm, t + h, Xn, prec[4])
     Dv = hs * (st(E[0]) * K1 + st(E[1]) * K2 + st(E[2]) * K3 + st(E[3]) * K4)
     return Xn, K4, error_norm(X, Xn, Dv, rtol, atol), (K2, K3)
 
@@ -151,7 +159,7 @@ def initial_step(sysm, t0, y0, f0, rtol, atol, hmax, prec):
     h0 = 0.01 * d0 / d1 if (d0 >= 1e-5 and d1 >= 1e-5) else 1e-6
     st = y0.dtype.type
     y1 = y0 + st(h0) * f0
-    f1 = models.rhs(sysm, t0 + h0, y1, prec)
+    f1 = _rhs(sysm, t0 + h0, y1, prec)
     d2 = float(np.max(np.abs(f1.astype(np.float64) - f0.astype(np.float64)) / sc)) / h0
     m = max(d1, d2)
     h1 = (0.01 / m) ** (1.0 / 3.0) if m > 1e-15 else max(1e-6, h0 * 1e-3)
@@ -184,7 +192,7 @@ def solve(sysm: models.System, t0: float, t1: float, y0: np.ndarray, rtol: float
     X = np.asarray(y0, dtype=np.float64).astype(state_t)
     if not np.all(np.isfinite(X)):
         return Result(X.astype(np.float64), t0, y_out, 0, 0, 0, ERR_NONFINITE, 0.0)
-    K1 = models.rhs(sysm, t0, X, prec[4])
+    K1 = _rhs(sysm, t0, X, prec[4])
     n_rhs = 1
     if h_init is None:
         h = initial_step(sysm, t0, X, K1, rtol, atol, hmax, prec[4])

@@ -216,6 +216,34 @@ def rhs(sysm: System, t: float, y: np.ndarray, prec: Sequence[str] = ("D", "D", 
 
 
 # --------------------------------------------------------------------------
+# Tensor-core variant of Kuramoto (ensembles sharing K): the weights and the
+# j-side sine/cosine are split into bfloat16 pairs x = x_hi + x_lo, the three
+# products K_hi s_hi + K_hi s_lo + K_lo s_hi are exact and summed (here in
+# binary64), the sums are held in binary32, the i-side finish is binary32 and
+# F = omega in binary64.
+# --------------------------------------------------------------------------
+
+def split_bf16(x32: np.ndarray):
+    hi = formats.round_bf16(np.asarray(x32, dtype=F32))
+    lo = formats.round_bf16((np.asarray(x32, dtype=F32) - hi).astype(F32))
+    return hi.astype(F64), lo.astype(F64)
+
+
+def rhs_tensor(sysm: System, t: float, y: np.ndarray) -> np.ndarray:
+    if sysm.kind != "kuramoto":
+        raise ValueError("the tensor-core variant is defined for Kuramoto ensembles")
+    kh, kl = split_bf16(sysm.q.astype(F32))
+    th = np.asarray(y, dtype=F64)
+    sj, cj = np.sin(th).astype(F32), np.cos(th).astype(F32)
+    sh, sl = split_bf16(sj)
+    ch, cl = split_bf16(cj)
+    S = (kh @ sh + kh @ sl + kl @ sh).astype(F32)
+    C = (kh @ ch + kh @ cl + kl @ ch).astype(F32)
+    coupling = cj * S - sj * C
+    return sysm.params + coupling.astype(F64)
+
+
+# --------------------------------------------------------------------------
 # Pairwise definitions (Eq. LCO, Eq. Kuramoto, Eq. CC) for brute-force pins.
 # --------------------------------------------------------------------------
 

@@ -37,6 +37,7 @@ EXPORTED = (
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
+    "bs3_ensemble_solve",
 )
 MLP_PARAMS = 1313
 MLP_MODEL = 1325
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_mlp_grad": (I, [P, P, P, I64, P, P]),
         "bs3_set_proposer": (I, [P, P]),
         "bs3_tc_gemm": (I, [I64, I64, I64, P, P, P]),
+        "bs3_ensemble_solve": (I, [P, I64, I64, P, P, D, D, D, D, P, P, P, P, ctypes.POINTER(I64), P]),
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
@@ -243,6 +245,18 @@ def bs3_set_proposer(sys_: int, model) -> int:
 
 def bs3_tc_gemm(M: int, Nc: int, K: int, A, B, C) -> int:
     return load().bs3_tc_gemm(M, Nc, K, _ptr(A), _ptr(B), _ptr(C))
+
+
+def bs3_ensemble_solve(K, N: int, T: int, omega, theta0, t0: float, t1: float, rtol: float, atol: float,
+                       theta_out, stream: int = 0):
+    """Returns (rc, n_acc[T], n_rej[T], status[T], lockstep_attempts)."""
+    n_acc = np.zeros(T, dtype=np.int64)
+    n_rej = np.zeros(T, dtype=np.int64)
+    status = np.zeros(T, dtype=np.int32)
+    steps = ctypes.c_int64()
+    rc = load().bs3_ensemble_solve(_ptr(K), N, T, _ptr(omega), _ptr(theta0), t0, t1, rtol, atol, _ptr(theta_out),
+                                   _ptr(n_acc), _ptr(n_rej), _ptr(status), ctypes.byref(steps), stream or None)
+    return rc, n_acc, n_rej, status, steps.value
 
 
 def bs3_destroy_system(sys_: int) -> int:

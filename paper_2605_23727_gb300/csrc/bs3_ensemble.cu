@@ -1,0 +1,417 @@
+// Lock-step ensembles of Kuramoto trajectories that share one coupling matrix
+// (the build's batched extension of the paper's solver).  Every stage of every
+// live trajectory is one tensor-core product
+//   [S_b | C_b]_i = sum_j K_ij [sin Y_bj | cos Y_bj]      (b = trajectory)
+// with K and the j-vectors split into bfloat16 pairs (bs3_tc.cuh), and the
+// stage epilogue (agent term, i-side finish, stage combinations, next j-vector,
+// error norm) fused into the tensor-memory readout.  Each trajectory keeps its
+// own t, h and accept/reject decision (the controller of the single-trajectory
+// solver), so the batch runs in lock step only at the level of attempts.
+//
+// Layout: states [T][N] (trajectory-major), j-vector operand [2T][N] with the
+// rows of trajectory b at 2b (sine) and 2b+1 (cosine), so that a 256-column
+// output tile holds both halves of 128 trajectories.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/bs3.h"
+#include "bs3_device.cuh"
+#include "bs3_tc.cuh"
+#include "bs3_tc_host.h"
+
+namespace bs3 {
+namespace ens {
+
+enum EPhase { E_K1 = 0, E_F1 = 1, E_B2 = 2, E_B3 = 3, E_B4 = 4 };
+
+struct Traj {
+  double *t, *h, *h0, *c21, *c32, *hs;
+  int *live, *xsel, *ksel, *last, *rej, *status;
+  long long *n_acc, *n_rej, *n_rhs;
+  unsigned long long *emax, *red0, *red1, *red2;
+  int* any_live;
+};
+
+struct EArgs {
+  int N, T, phase;
+  const double* omega;   // [T][N]
+  double* X;             // [2][T][N]
+  double* K14;           // [2][T][N]: K1 and K4 slots
+  double* K2;            // [T][N]
+  double* K3;            // [T][N]
+  __nv_bfloat16* Vh;     // [2T][N]
+  __nv_bfloat16* Vl;     // [2T][N]
+  Traj tr;
+  double rtol, atol, t1, hmax, hmin;
+  long long max_attempts, max_rejects;
+};
+
+constexpr double kB1 = 2.0 / 9.0, kB2 = 1.0 / 3.0, kB3 = 4.0 / 9.0;
+constexpr double kE1 = -5.0 / 72.0, kE2 = 1.0 / 12.0, kE3 = 1.0 / 9.0, kE4 = -1.0 / 8.0;
+
+__device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
+  float s, c;
+  sincos_f_of_d(y, &s, &c);
+  const __nv_bfloat16 sh = __float2bfloat16_rn(s), ch = __float2bfloat16_rn(c);
+  const size_t rs = (size_t)(2 * b) * a.N + i, rc = rs + a.N;
+  a.Vh[rs] = sh;
+  a.Vl[rs] = __float2bfloat16_rn(s - __bfloat162float(sh));
+  a.Vh[rc] = ch;
+  a.Vl[rc] = __float2bfloat16_rn(c - __bfloat162float(ch));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  unsigned long long x = (unsigned long long)__double_as_longlong(fabs(v));
+  if (v != v) x = 0x7ff8000000000000ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, x, off);
+    x = o > x ? o : x;
+  }
+  return __longlong_as_double((long long)x);
+}
+
+// The stage epilogue run on the accumulator rows of one 128 x 256 tile.
+struct Epilogue {
+  EArgs a;
+  __device__ void operator()(int i, int col0, const float* v) const {
+    const int lane = threadIdx.x & 31;
+    const int N = a.N, T = a.T;
+    (void)T;
+    for (int j = 0; j < 16; ++j) {
+      const int b = col0 / 2 + j;
+      if (!a.tr.live[b]) continue;   // uniform over the warp
+      const size_t o = (size_t)b * N + i;
+      const size_t slot = (size_t)T * N;
+      const int xs = a.tr.xsel[b], ks = a.tr.ksel[b];
+      const double x = a.X[xs * slot + o];
+      const double k1 = a.K14[ks * slot + o];
+      double y;
+      switch (a.phase) {
+        case E_K1: y = x; break;
+        case E_F1: y = x + a.tr.h0[b] * k1; break;
+        case E_B2: y = x + a.tr.c21[b] * k1; break;
+        case E_B3: y = x + a.tr.c32[b] * a.K2[o]; break;
+        default: y = a.X[(1 - xs) * slot + o]; break;
+      }
+      float si, ci;
+      sincos_f_of_d(y, &si, &ci);
+      const float cpl = ci * v[2 * j] - si * v[2 * j + 1];
+      const double k = a.omega[o] + (double)cpl;
+      const double thr = a.atol / a.rtol;
+      double m = 0.0;
+      switch (a.phase) {
+        case E_K1: {
+          a.K14[ks * slot + o] = k;
+          const double sc = a.rtol * fmax(fabs(x), thr);
+          double m0 = warp_max(fabs(x) / sc), m1 = warp_max(fabs(k) / sc);
+          if (lane == 0) {
+            atomicMax(&a.tr.red0[b], (unsigned long long)__double_as_longlong(m0));
+            atomicMax(&a.tr.red1[b], (unsigned long long)__double_as_longlong(m1));
+          }
+          break;
+        }
+        case E_F1: {
+          const double sc = a.rtol * fmax(fabs(x), thr);
+          m = warp_max(fabs(k - k1) / sc);
+          if (lane == 0) atomicMax(&a.tr.red2[b], (unsigned long long)__double_as_longlong(m));
+          break;
+        }
+        case E_B2:
+          a.K2[o] = k;
+          put_v(a, b, i, x + a.tr.c32[b] * k);
+          break;
+        case E_B3: {
+          a.K3[o] = k;
+          const double xn = x + a.tr.hs[b] * ((kB1 * k1 + kB2 * a.K2[o]) + kB3 * k);
+          a.X[(1 - xs) * slot + o] = xn;
+          put_v(a, b, i, xn);
+          break;
+        }
+        default: {
+          a.K14[(1 - ks) * slot + o] = k;
+          const double dv = a.tr.hs[b] * (((kE1 * k1 + kE2 * a.K2[o]) + kE3 * a.K3[o]) + kE4 * k);
+          const double w = fmax(fmax(fabs(x), fabs(y)), thr);
+          double e = fabs(dv) / w;
+          if (!isfinite(y) || !isfinite(k)) e = __longlong_as_double(0x7ff8000000000000ll);
+          m = warp_max(e);
+          if (lane == 0) atomicMax(&a.tr.emax[b], (unsigned long long)__double_as_longlong(m));
+          break;
+        }
+      }
+    }
+  }
+};
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    ens_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, EArgs a, int K,
+                    int* err, long long spin) {
+  const Epilogue epi{a};
+  tc::gemm_tile(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, epi, err, spin);
+}
+
+// j-vector operand of the stage argument Y = X + c K1 (c = 0, h0 or h/2).
+__global__ void ens_prologue(EArgs a, int which) {
+  const size_t n = (size_t)a.T * a.N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / a.N), i = (int)(e % a.N);
+    if (!a.tr.live[b]) continue;
+    const size_t slot = (size_t)a.T * a.N;
+    const double x = a.X[a.tr.xsel[b] * slot + e];
+    const double k1 = a.K14[a.tr.ksel[b] * slot + e];
+    const double c = which == 0 ? 0.0 : (which == 1 ? a.tr.h0[b] : a.tr.c21[b]);
+    put_v(a, b, i, which == 0 ? x : x + c * k1);
+  }
+}
+
+__device__ __forceinline__ double bits(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+// Sets up the next attempt of trajectory b (h clamp, last-step stretch,
+// failure conditions of Sec. 2.2) or retires it.
+__device__ __forceinline__ void next_attempt(const EArgs& a, int b) {
+  const Traj& r = a.tr;
+  if (!(r.t[b] < a.t1)) { r.live[b] = 0; return; }
+  if (r.n_rej[b] > a.max_rejects) { r.status[b] = S_MAX_REJECTS; r.live[b] = 0; return; }
+  if (r.n_acc[b] + r.n_rej[b] >= a.max_attempts) { r.status[b] = S_MAX_STEPS; r.live[b] = 0; return; }
+  double h = fmin(r.h[b], a.hmax);
+  if (h <= a.hmin) { r.status[b] = S_STEP_TOO_SMALL; r.live[b] = 0; return; }
+  r.last[b] = (r.t[b] + 1.1 * h >= a.t1);
+  if (r.last[b]) h = a.t1 - r.t[b];
+  r.h[b] = h;
+  r.hs[b] = h;
+  r.c21[b] = 0.5 * h;
+  r.c32[b] = 0.75 * h;
+}
+
+// stage: 0 after K1 (h0 from d0, d1), 1 after F1 (starting step), 2 after an attempt.
+__global__ void ens_control(EArgs a, int stage) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  int live = 0;
+  if (b < a.T) {
+    const Traj& r = a.tr;
+    if (r.live[b]) {
+      if (stage == 0) {
+        const double d0 = bits(r.red0[b]), d1 = bits(r.red1[b]);
+        r.n_rhs[b] = 1;
+        if (d0 != d0 || isinf(d0) || d1 != d1 || isinf(d1)) {
+          r.status[b] = S_NONFINITE;
+          r.live[b] = 0;
+        } else {
+          r.h0[b] = (d0 >= 1e-5 && d1 >= 1e-5) ? 0.01 * d0 / d1 : 1e-6;
+        }
+      } else if (stage == 1) {
+        r.n_rhs[b] = 2;
+        const double h0 = r.h0[b];
+        const double d1 = bits(r.red1[b]), d2 = bits(r.red2[b]) / h0;
+        const double m = fmax(d1, d2);
+        const double h1 = (m > 1e-15) ? pow(0.01 / m, 1.0 / 3.0) : fmax(1e-6, h0 * 1e-3);
+        r.h[b] = fmin(fmin(100.0 * h0, h1), a.hmax);
+        next_attempt(a, b);
+      } else {
+        const double E = bits(r.emax[b]);
+        r.emax[b] = 0ull;
+        r.n_rhs[b] += 3;
+        if (E != E || isinf(E)) {
+          r.status[b] = S_NONFINITE;
+          ++r.n_rej[b];
+          r.live[b] = 0;
+        } else {
+          const double h = r.h[b];
+          if (E <= a.rtol) {
+            r.t[b] = r.last[b] ? a.t1 : r.t[b] + h;
+            r.xsel[b] ^= 1;
+            r.ksel[b] ^= 1;
+            ++r.n_acc[b];
+            double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * pow(a.rtol / E, 1.0 / 3.0));
+            if (r.rej[b]) fac = fmin(1.0, fac);
+            r.h[b] = h * fac;
+            r.rej[b] = 0;
+          } else {
+            ++r.n_rej[b];
+            r.h[b] = r.rej[b] ? h * 0.5 : h * fmax(0.5, 0.8 * pow(a.rtol / E, 1.0 / 3.0));
+            r.rej[b] = 1;
+          }
+          next_attempt(a, b);
+        }
+      }
+      live = r.live[b];
+    }
+  }
+  live = __syncthreads_or(live);
+  if (threadIdx.x == 0 && live) atomicOr(a.tr.any_live, 1);
+}
+
+__global__ void ens_gather(EArgs a, double* out) {
+  const size_t n = (size_t)a.T * a.N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / a.N);
+    out[e] = a.X[(size_t)a.tr.xsel[b] * n + e];
+  }
+}
+
+}  // namespace ens
+}  // namespace bs3
+
+using namespace bs3;
+using namespace bs3::ens;
+
+#define EN_CUDA(call)                                     \
+  do {                                                    \
+    if ((call) != cudaSuccess) { rc = BS3_ERR_CUDA; goto done; } \
+  } while (0)
+#define EN_RC(expr)                \
+  do {                             \
+    rc = (expr);                   \
+    if (rc != BS3_OK) goto done;   \
+  } while (0)
+
+extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                                  double t0, double t1, double rtol, double atol, double* theta_out,
+                                  int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
+                                  void* stream_) {
+  if (!K || !omega || !theta0 || !theta_out) return BS3_ERR_INVALID_ARG;
+  if (N < tc::BM || N % tc::BM || N % tc::BK || T < tc::BN / 2 || (2 * T) % tc::BN) return BS3_ERR_INVALID_ARG;
+  if (N > (1 << 20) || T > (1 << 16)) return BS3_ERR_INVALID_ARG;
+  if (!(t1 > t0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream_;
+  cudaStream_t own = nullptr;   // graphs cannot be captured on the legacy default stream
+  int rc = BS3_OK;
+  const size_t NN = (size_t)N * N, TN = (size_t)T * N;
+  void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr;
+  double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *K3 = nullptr, *dsc = nullptr;
+  int *isc = nullptr, *derr = nullptr;
+  long long* lsc = nullptr;
+  unsigned long long* usc = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  EArgs a;
+  std::memset(&a, 0, sizeof(a));
+  int herr = 0, any = 1;
+  long long iters = 0;
+  const int U = 8;   // attempts per graph launch
+  const dim3 ggrid((unsigned)(N / tc::BM), (unsigned)(2 * T / tc::BN));
+  const unsigned ctl_blocks = (unsigned)((T + 255) / 256);
+  const unsigned ew_blocks = (unsigned)std::min<size_t>((TN + 255) / 256, 152 * 16);
+  if (st == nullptr) {
+    EN_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    EN_CUDA(cudaDeviceSynchronize());   // the caller's legacy-stream work is complete
+    st = own;
+  }
+  EN_CUDA(cudaMalloc(&kh, NN * 2));
+  EN_CUDA(cudaMalloc(&kl, NN * 2));
+  EN_CUDA(cudaMalloc(&vh, 2 * TN * 2));
+  EN_CUDA(cudaMalloc(&vl, 2 * TN * 2));
+  EN_CUDA(cudaMalloc(&X, 2 * TN * sizeof(double)));
+  EN_CUDA(cudaMalloc(&K14, 2 * TN * sizeof(double)));
+  EN_CUDA(cudaMalloc(&K2, TN * sizeof(double)));
+  EN_CUDA(cudaMalloc(&K3, TN * sizeof(double)));
+  EN_CUDA(cudaMalloc(&dsc, 6 * T * sizeof(double)));
+  EN_CUDA(cudaMalloc(&isc, (6 * T + 1) * sizeof(int)));
+  EN_CUDA(cudaMalloc(&lsc, 3 * T * sizeof(long long)));
+  EN_CUDA(cudaMalloc(&usc, 4 * T * sizeof(unsigned long long)));
+  EN_CUDA(cudaMalloc(&derr, sizeof(int)));
+  EN_CUDA(cudaMemsetAsync(vh, 0, 2 * TN * 2, st));
+  EN_CUDA(cudaMemsetAsync(vl, 0, 2 * TN * 2, st));
+  EN_CUDA(cudaMemsetAsync(isc, 0, (6 * T + 1) * sizeof(int), st));
+  EN_CUDA(cudaMemsetAsync(lsc, 0, 3 * T * sizeof(long long), st));
+  EN_CUDA(cudaMemsetAsync(usc, 0, 4 * T * sizeof(unsigned long long), st));
+  EN_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
+  EN_CUDA(cudaMemcpyAsync(X, theta0, TN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  EN_RC(tc_split(K, NN, kh, kl, st));
+  EN_RC(tc_encode_bf16_2d(&mAh, kh, N, N, tc::BM));
+  EN_RC(tc_encode_bf16_2d(&mAl, kl, N, N, tc::BM));
+  EN_RC(tc_encode_bf16_2d(&mBh, vh, 2 * T, N, tc::BN));
+  EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, tc::BN));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  a.N = (int)N;
+  a.T = (int)T;
+  a.omega = omega;
+  a.X = X;
+  a.K14 = K14;
+  a.K2 = K2;
+  a.K3 = K3;
+  a.Vh = (__nv_bfloat16*)vh;
+  a.Vl = (__nv_bfloat16*)vl;
+  a.tr.t = dsc; a.tr.h = dsc + T; a.tr.h0 = dsc + 2 * T; a.tr.c21 = dsc + 3 * T; a.tr.c32 = dsc + 4 * T;
+  a.tr.hs = dsc + 5 * T;
+  a.tr.live = isc; a.tr.xsel = isc + T; a.tr.ksel = isc + 2 * T; a.tr.last = isc + 3 * T; a.tr.rej = isc + 4 * T;
+  a.tr.status = isc + 5 * T; a.tr.any_live = isc + 6 * T;
+  a.tr.n_acc = lsc; a.tr.n_rej = lsc + T; a.tr.n_rhs = lsc + 2 * T;
+  a.tr.emax = usc; a.tr.red0 = usc + T; a.tr.red1 = usc + 2 * T; a.tr.red2 = usc + 3 * T;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.t1 = t1;
+  a.hmax = 0.1 * (t1 - t0);
+  a.hmin = 100.0 * DBL_EPSILON;
+  a.max_attempts = 100000;
+  a.max_rejects = 85000;
+  {
+    // t = t0 and every trajectory live
+    std::vector<double> tt(T, t0);
+    std::vector<int> ones(T, 1);
+    EN_CUDA(cudaMemcpyAsync(a.tr.t, tt.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
+    EN_CUDA(cudaMemcpyAsync(a.tr.live, ones.data(), T * sizeof(int), cudaMemcpyHostToDevice, st));
+    EN_CUDA(cudaStreamSynchronize(st));
+  }
+  // ---- K1 = f(t0, y0) and the starting step of every trajectory
+  ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
+  a.phase = E_K1;
+  ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
+  ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
+  a.phase = E_F1;
+  ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
+  EN_CUDA(cudaGetLastError());
+  // ---- U attempts per graph: prologue (Y2), three fused stages, control
+  EN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  for (int u = 0; u < U; ++u) {
+    ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 2);
+    a.phase = E_B2;
+    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    a.phase = E_B3;
+    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    a.phase = E_B4;
+    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
+    ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
+  }
+  EN_CUDA(cudaStreamEndCapture(st, &graph));
+  EN_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  while (any) {
+    EN_CUDA(cudaGraphLaunch(exec, st));
+    EN_CUDA(cudaMemcpyAsync(&any, a.tr.any_live, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EN_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EN_CUDA(cudaStreamSynchronize(st));
+    iters += U;
+    if (herr) { rc = BS3_ERR_DEVICE_WAIT; break; }
+    if (iters > a.max_attempts + U) break;
+  }
+  ens_gather<<<ew_blocks, 256, 0, st>>>(a, theta_out);
+  EN_CUDA(cudaGetLastError());
+  EN_CUDA(cudaStreamSynchronize(st));
+  if (n_acc) EN_CUDA(cudaMemcpy(n_acc, a.tr.n_acc, T * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (n_rej) EN_CUDA(cudaMemcpy(n_rej, a.tr.n_rej, T * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (status) EN_CUDA(cudaMemcpy(status, a.tr.status, T * sizeof(int), cudaMemcpyDeviceToHost));
+  if (lockstep_attempts) *lockstep_attempts = iters;
+done:
+  if (own) {
+    cudaStreamSynchronize(own);
+    cudaStreamDestroy(own);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
+  cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
+  return rc;
+}

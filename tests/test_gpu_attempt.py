@@ -22,7 +22,7 @@ def _wl(kind, N):
 
 
 @pytest.mark.parametrize("kind", models.KINDS)
-@pytest.mark.parametrize("variant", list(obs3.VARIANTS))
+@pytest.mark.parametrize("variant", list(obs3.PAPER_VARIANTS))
 @pytest.mark.parametrize("accum", ["float2", "f64"])
 def test_attempt_matches_oracle(kind, variant, accum):
     bs3 = library()

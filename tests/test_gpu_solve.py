@@ -34,7 +34,7 @@ def _compare(w, store, variant, accum="float2", t_out=None, exact_y=None, reside
     return st, y, y_out, ref, diff
 
 
-@pytest.mark.parametrize("variant", list(obs3.VARIANTS))
+@pytest.mark.parametrize("variant", list(obs3.PAPER_VARIANTS))
 @pytest.mark.parametrize("accum", ["float2", "f64"])
 def test_lco_config_n256_all_variants(variant, accum):
     """Second-order oscillators, N = 256, rtol = atol = 1e-6, t in [0, 10]."""

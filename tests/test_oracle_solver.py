@@ -173,7 +173,7 @@ def test_precision_plateaus_follow_the_paper():
     w, S = _lco(64)
     ex = exact.lco_cfg_exact(w.params, w.coupling, w.y0[:64], w.y0[64:], w.t1)
     err = {v: metrics.normalized_final_error(ex, bs3.solve(S, 0.0, w.t1, w.y0, 1e-9, 1e-9, v).y, 64)
-           for v in bs3.VARIANTS}
+           for v in bs3.PAPER_VARIANTS}
     assert err["double"] < 2e-8
     assert err["mixed2"] < 10 * err["double"] + 5e-8
     assert err["mixed1"] > 3 * err["mixed2"]
