@@ -265,6 +265,22 @@ int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega
                        double t0, double t1, double rtol, double atol, double* theta_out, int64_t* n_acc,
                        int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream);
 
+/* Ragged batch of S independent systems of one kind (sizes N_k may all
+ * differ) solved in one launch (the build's batched extension): each CTA takes
+ * whole systems from a work queue, largest first, and runs the solver of
+ * bs3_solve on it with CTA barriers only; every system has its own adaptive
+ * h, t1 and status.  All host arrays, concatenated over the systems in order:
+ *   Ns[S]; params: the per-agent values of each system (N_k values; for
+ *   BS3_CIRCADIAN N_k values then the 8 constants, which must agree across the
+ *   batch; NULL for BS3_LCO_PAPER); K: each system's N_k x N_k binary32
+ *   row-major weights; y0, y_final: each system's d*N_k state (SoA);
+ *   t0[S], t1[S]; stats[S] (may be NULL).
+ * store, rtol, atol, variant, accum as bs3_set_coupling / bs3_solve (wall-clock
+ * limits not enforced).  Returns the first non-OK system status, else BS3_OK. */
+int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params, const float* K, int store,
+                    const double* y0, const double* t0, const double* t1, double rtol, double atol, int variant,
+                    int accum, double* y_final, bs3_stats* stats, int device, void* stream);
+
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384
 

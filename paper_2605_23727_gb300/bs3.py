@@ -37,7 +37,7 @@ EXPORTED = (
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
-    "bs3_ensemble_solve",
+    "bs3_ensemble_solve", "bs3_batch_solve",
 )
 MLP_PARAMS = 1313
 MLP_MODEL = 1325
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_set_proposer": (I, [P, P]),
         "bs3_tc_gemm": (I, [I64, I64, I64, P, P, P]),
         "bs3_ensemble_solve": (I, [P, I64, I64, P, P, D, D, D, D, P, P, P, P, ctypes.POINTER(I64), P]),
+        "bs3_batch_solve": (I, [I, I64, P, P, P, I, P, P, P, D, D, I, I, P, P, I, P]),
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
@@ -257,6 +258,23 @@ def bs3_ensemble_solve(K, N: int, T: int, omega, theta0, t0: float, t1: float, r
     rc = load().bs3_ensemble_solve(_ptr(K), N, T, _ptr(omega), _ptr(theta0), t0, t1, rtol, atol, _ptr(theta_out),
                                    _ptr(n_acc), _ptr(n_rej), _ptr(status), ctypes.byref(steps), stream or None)
     return rc, n_acc, n_rej, status, steps.value
+
+
+def bs3_batch_solve(kind: int, Ns, params, K, store: int, y0, t0, t1, rtol: float, atol: float, variant: int,
+                    accum: int, device: int = 0, stream: int = 0):
+    """Host arrays in, returns (rc, y_final concat, stats list)."""
+    Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+    S = Ns.size
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.float32)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    t0 = np.ascontiguousarray(t0, dtype=np.float64)
+    t1 = np.ascontiguousarray(t1, dtype=np.float64)
+    yf = np.zeros_like(y0)
+    stats = (bs3_stats * S)()
+    rc = load().bs3_batch_solve(kind, S, _ptr(Ns), _ptr(p), _ptr(K), store, _ptr(y0), _ptr(t0), _ptr(t1), rtol, atol,
+                                variant, accum, _ptr(yf), ctypes.cast(stats, ctypes.c_void_p), device, stream or None)
+    return rc, yf, list(stats)
 
 
 def bs3_destroy_system(sys_: int) -> int:

@@ -400,6 +400,172 @@ int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_param
   return BS3_OK;
 }
 
+int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params, const float* K, int store,
+                    const double* y0, const double* t0, const double* t1, double rtol, double atol, int variant,
+                    int accum, double* y_final, bs3_stats* stats, int device, void* stream_) {
+  if (kind < BS3_LCO_CFG || kind > BS3_CIRCADIAN || S < 1 || S > (1 << 24) || !Ns || !K || !y0 || !t0 || !t1 ||
+      !y_final)
+    return BS3_ERR_INVALID_ARG;
+  if (store < BS3_F64 || store > BS3_FP8E4M3 || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
+  if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64)
+    return BS3_ERR_INVALID_ARG;
+  if (kind != BS3_LCO_PAPER && !params) return BS3_ERR_INVALID_ARG;
+  const int d = (kind == BS3_KURAMOTO) ? 1 : (kind == BS3_CIRCADIAN ? 4 : 2);
+  const int per_agent = (kind == BS3_LCO_PAPER) ? 0 : 1;
+  std::vector<int64_t> offN(S + 1, 0), offK(S + 1, 0), offQ(S + 1, 0), offL(S + 1, 0);
+  for (int64_t k = 0; k < S; ++k) {
+    if (Ns[k] < 1 || Ns[k] > (1 << 20) || !(t1[k] > t0[k])) return BS3_ERR_INVALID_ARG;
+    const int64_t ld = (Ns[k] + 15) / 16 * 16;
+    offN[k + 1] = offN[k] + Ns[k];
+    offK[k + 1] = offK[k] + Ns[k] * Ns[k];
+    offQ[k + 1] = offQ[k] + Ns[k] * ld;
+    offL[k + 1] = offL[k] + ld;
+  }
+  const int64_t TN = offN[S];
+  // circadian: 8 constants after each system's k1 values (params concat: N_k + 8 per system)
+  std::vector<int64_t> offP(S + 1, 0);
+  for (int64_t k = 0; k < S; ++k) offP[k + 1] = offP[k] + (kind == BS3_CIRCADIAN ? Ns[k] + 8 : per_agent * Ns[k]);
+  DeviceGuard guard(device);
+  cudaStream_t st = (cudaStream_t)stream_;
+  int rc = BS3_OK;
+  unsigned char* arena = nullptr;
+  float* kdev = nullptr;
+  float* amax = nullptr;
+  // arena layout
+  const size_t eb = store_bytes(store);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oQ = take((size_t)offQ[S] * eb), oScale = take(TN * 4), oRow = take(TN * 8), oPar = take(TN * 8),
+               oTh = take(TN * 8), oY0 = take((size_t)d * TN * 8), oYF = take((size_t)d * TN * 8),
+               oState = take((size_t)6 * d * TN * 8), oJ32 = take((size_t)6 * offL[S] * 4),
+               oJ64 = take((size_t)6 * offL[S] * 8), oCtl = take((size_t)S * sizeof(Control)),
+               oDesc = take((size_t)S * sizeof(SysDesc)), oNext = take(sizeof(int));
+  std::vector<SysDesc> desc(S);
+  std::vector<int64_t> order(S);
+  std::vector<double> par_h(TN), th_h(TN);
+  std::vector<Control> ctl(S);
+  int64_t maxNN = 0, maxN = 0;
+  for (int64_t k = 0; k < S; ++k) {
+    maxNN = std::max(maxNN, Ns[k] * Ns[k]);
+    maxN = std::max(maxN, Ns[k]);
+  }
+  if (cudaMalloc(&arena, off) != cudaSuccess) return BS3_ERR_CUDA;
+  if (cudaMalloc(&kdev, (size_t)maxNN * 4) != cudaSuccess) { cudaFree(arena); return BS3_ERR_CUDA; }
+  if (cudaMalloc(&amax, (size_t)maxN * 4) != cudaSuccess) {
+    cudaFree(arena); cudaFree(kdev); return BS3_ERR_CUDA;
+  }
+  do {
+    if (cudaMemsetAsync(arena + oJ32, 0, (size_t)6 * offL[S] * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(arena + oJ64, 0, (size_t)6 * offL[S] * 8, st) != cudaSuccess ||
+        cudaMemsetAsync(arena + oCtl, 0, (size_t)S * sizeof(Control), st) != cudaSuccess ||
+        cudaMemsetAsync(arena + oNext, 0, sizeof(int), st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    // per-agent parameters (and k1/(k0-k1) for the circadian kind)
+    double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = 0; k < S; ++k) {
+      for (int64_t i = 0; i < Ns[k]; ++i) {
+        const double pv = per_agent ? params[offP[k] + i] : 0.0;
+        par_h[offN[k] + i] = pv;
+        if (kind == BS3_CIRCADIAN) {
+          for (int q = 0; q < 8; ++q) g[q] = params[offP[k] + Ns[k] + q];
+          th_h[offN[k] + i] = pv / (g[0] - pv);
+        } else {
+          th_h[offN[k] + i] = 0.0;
+        }
+      }
+    }
+    if (cudaMemcpyAsync(arena + oPar, par_h.data(), TN * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(arena + oTh, th_h.data(), TN * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(arena + oY0, y0, (size_t)d * TN * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = BS3_ERR_CUDA; break;
+    }
+    // quantise each system's weights into its slice of the arena
+    for (int64_t k = 0; k < S && rc == BS3_OK; ++k) {
+      const int64_t N = Ns[k], ld = (N + 15) / 16 * 16;
+      float* sc = (float*)(arena + oScale) + offN[k];
+      void* q = arena + oQ + (size_t)offQ[k] * eb;
+      if (cudaMemcpyAsync(kdev, K + offK[k], (size_t)N * N * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = BS3_ERR_CUDA; break;
+      }
+      const int blocks = (int)std::min<int64_t>((N * ld + 255) / 256, 152 * 64);
+      row_amax_kernel<float><<<(unsigned)N, 256, 0, st>>>(kdev, N, amax);
+      scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(amax, N, store, sc);
+      quantize_kernel<float><<<blocks, 256, 0, st>>>(kdev, N, ld, store, 0, sc, q);
+      rowsum_kernel<<<(unsigned)N, 256, 0, st>>>(q, store, N, ld, sc, (double*)(arena + oRow) + offN[k]);
+      if (cudaGetLastError() != cudaSuccess) rc = BS3_ERR_CUDA;
+    }
+    if (rc != BS3_OK) break;
+    // descriptors, largest systems first (longest-processing-time order)
+    for (int64_t k = 0; k < S; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return Ns[x] > Ns[y]; });
+    for (int64_t r = 0; r < S; ++r) {
+      const int64_t k = order[r];
+      SysDesc& D = desc[r];
+      D.N = (int)Ns[k];
+      D.ld = (int)((Ns[k] + 15) / 16 * 16);
+      D.q = arena + oQ + (size_t)offQ[k] * eb;
+      D.scale = (const float*)(arena + oScale) + offN[k];
+      D.rowsum = (const double*)(arena + oRow) + offN[k];
+      D.par = (const double*)(arena + oPar) + offN[k];
+      D.theta_h = (kind == BS3_CIRCADIAN) ? (const double*)(arena + oTh) + offN[k] : nullptr;
+      D.y0 = (const double*)(arena + oY0) + (size_t)d * offN[k];
+      D.y_final = (double*)(arena + oYF) + (size_t)d * offN[k];
+      D.state = (double*)(arena + oState) + (size_t)6 * d * offN[k];
+      D.jv32 = (float*)(arena + oJ32) + (size_t)6 * offL[k];
+      D.jv64 = (double*)(arena + oJ64) + (size_t)6 * offL[k];
+      D.ctrl = (Control*)(arena + oCtl) + k;
+      D.t0 = t0[k];
+      D.t1 = t1[k];
+    }
+    if (cudaMemcpyAsync(arena + oDesc, desc.data(), S * sizeof(SysDesc), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    BatchArgs ba;
+    std::memset(&ba, 0, sizeof(ba));
+    Args& a = ba.common;
+    a.variant = variant;
+    a.accum = accum;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.hmin = 100.0 * (variant == BS3_SINGLE ? (double)FLT_EPSILON : DBL_EPSILON);
+    a.max_attempts = 100000;
+    a.max_rejects = 85000;
+    a.spin_limit = 1;
+    a.l2_keep = 0;
+    if (kind == BS3_CIRCADIAN)
+      for (int q = 0; q < 8; ++q) a.g[q] = params[offP[0] + Ns[0] + q];   // constants shared by the batch
+    ba.sys = (const SysDesc*)(arena + oDesc);
+    ba.S = (int)S;
+    ba.next = (int*)(arena + oNext);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    const unsigned grid = (unsigned)std::min<int64_t>(sms, S);
+    void* kargs[] = {&ba};
+    if (cudaLaunchKernel(batch_kernel_lookup(kind, store), dim3(grid), dim3(kBlock), kargs, 0, st) != cudaSuccess) {
+      rc = BS3_ERR_CUDA; break;
+    }
+    if (cudaMemcpyAsync(y_final, arena + oYF, (size_t)d * TN * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(ctl.data(), arena + oCtl, S * sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    int worst = BS3_OK;
+    for (int64_t k = 0; k < S; ++k) {
+      if (stats) {
+        stats[k].n_accepted = ctl[k].n_acc;
+        stats[k].n_rejected = ctl[k].n_rej;
+        stats[k].n_rhs_evals = ctl[k].n_rhs;
+        stats[k].t_reached = ctl[k].t;
+        stats[k].h_last = ctl[k].h;
+        stats[k].status = ctl[k].status;
+        stats[k].n_out_written = 0;
+      }
+      if (ctl[k].status != BS3_OK && worst == BS3_OK) worst = ctl[k].status;
+    }
+    rc = worst;
+  } while (0);
+  cudaFree(arena);
+  cudaFree(kdev);
+  cudaFree(amax);
+  return rc;
+}
+
 int bs3_set_proposer(bs3_system_t s, const float* model) {
   if (!s) return BS3_ERR_INVALID_ARG;
   DeviceGuard guard(s->device);

@@ -3,25 +3,45 @@
 
 namespace bs3 {
 const void* kernel_lco_cfg_f64();
+const void* batch_kernel_lco_cfg_f64();
 const void* kernel_lco_cfg_f32();
+const void* batch_kernel_lco_cfg_f32();
 const void* kernel_lco_cfg_bf16();
+const void* batch_kernel_lco_cfg_bf16();
 const void* kernel_lco_cfg_f16();
+const void* batch_kernel_lco_cfg_f16();
 const void* kernel_lco_cfg_fp8();
+const void* batch_kernel_lco_cfg_fp8();
 const void* kernel_lco_paper_f64();
+const void* batch_kernel_lco_paper_f64();
 const void* kernel_lco_paper_f32();
+const void* batch_kernel_lco_paper_f32();
 const void* kernel_lco_paper_bf16();
+const void* batch_kernel_lco_paper_bf16();
 const void* kernel_lco_paper_f16();
+const void* batch_kernel_lco_paper_f16();
 const void* kernel_lco_paper_fp8();
+const void* batch_kernel_lco_paper_fp8();
 const void* kernel_kuramoto_f64();
+const void* batch_kernel_kuramoto_f64();
 const void* kernel_kuramoto_f32();
+const void* batch_kernel_kuramoto_f32();
 const void* kernel_kuramoto_bf16();
+const void* batch_kernel_kuramoto_bf16();
 const void* kernel_kuramoto_f16();
+const void* batch_kernel_kuramoto_f16();
 const void* kernel_kuramoto_fp8();
+const void* batch_kernel_kuramoto_fp8();
 const void* kernel_circadian_f64();
+const void* batch_kernel_circadian_f64();
 const void* kernel_circadian_f32();
+const void* batch_kernel_circadian_f32();
 const void* kernel_circadian_bf16();
+const void* batch_kernel_circadian_bf16();
 const void* kernel_circadian_f16();
+const void* batch_kernel_circadian_f16();
 const void* kernel_circadian_fp8();
+const void* batch_kernel_circadian_fp8();
 
 inline const void* kernel_lookup(int kind, int store) {
   static const void* (*const table[4][5])() = {
@@ -29,6 +49,16 @@ inline const void* kernel_lookup(int kind, int store) {
       {kernel_lco_paper_f64, kernel_lco_paper_f32, kernel_lco_paper_bf16, kernel_lco_paper_f16, kernel_lco_paper_fp8},
       {kernel_kuramoto_f64, kernel_kuramoto_f32, kernel_kuramoto_bf16, kernel_kuramoto_f16, kernel_kuramoto_fp8},
       {kernel_circadian_f64, kernel_circadian_f32, kernel_circadian_bf16, kernel_circadian_f16, kernel_circadian_fp8},
+  };
+  return table[kind][store]();
+}
+
+inline const void* batch_kernel_lookup(int kind, int store) {
+  static const void* (*const table[4][5])() = {
+      {batch_kernel_lco_cfg_f64, batch_kernel_lco_cfg_f32, batch_kernel_lco_cfg_bf16, batch_kernel_lco_cfg_f16, batch_kernel_lco_cfg_fp8},
+      {batch_kernel_lco_paper_f64, batch_kernel_lco_paper_f32, batch_kernel_lco_paper_bf16, batch_kernel_lco_paper_f16, batch_kernel_lco_paper_fp8},
+      {batch_kernel_kuramoto_f64, batch_kernel_kuramoto_f32, batch_kernel_kuramoto_bf16, batch_kernel_kuramoto_f16, batch_kernel_kuramoto_fp8},
+      {batch_kernel_circadian_f64, batch_kernel_circadian_f32, batch_kernel_circadian_bf16, batch_kernel_circadian_f16, batch_kernel_circadian_fp8},
   };
   return table[kind][store]();
 }

@@ -615,79 +615,41 @@ struct Scal {
   double theta[kThetaMax];
 };
 
-template <int KIND, int ST>
-__global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
+// Smallest warp groups (>= 32 threads) whose row blocks cover rc rows in one pass.
+template <int KIND>
+__device__ __forceinline__ int group_threads(int rc) {
+  constexpr int RBk = rows_per_tile(KIND);
+  int gt = kBlock / 4;
+  while (gt > 32 && (kBlock / gt) * RBk < rc) gt >>= 1;
+  return gt;
+}
+
+// Grid-wide barrier (persistent launch over all SMs) or CTA barrier (a CTA
+// that solves one system alone).
+template <bool CTA>
+__device__ __forceinline__ bool sync_all(Control* c, unsigned long long& target, long long spin_limit, int* s_abort) {
+  if (CTA) {
+    __syncthreads();
+    return true;
+  }
+  return grid_sync(c, target, spin_limit, s_abort);
+}
+
+// A job (RHS, one attempt or a whole solve) on the agents [x.rb, x.rb + x.nr)
+// whose state x already holds.  CTA = false: the agents of one system are
+// spread over the whole grid; CTA = true: this CTA owns all of them.
+template <int KIND, int ST, bool CTA>
+__device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_abort, unsigned long long* s_red,
+                                        unsigned long long* s_grp, const float* smlp) {
   constexpr int d = Dim<KIND>::d;
-  extern __shared__ __align__(128) unsigned char dyn[];
-  __shared__ int s_abort;
-  __shared__ unsigned long long s_red[kBlock / 32];
-  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
-  __shared__ Scal sc;
   const int N = a.N;
-  const int G = gridDim.x, b = blockIdx.x;
+  const int b = blockIdx.x;
   const int tid = threadIdx.x;
+  const bool leader = CTA ? (tid == 0) : (b == 0 && tid == 0);
   Control* ctrl = a.ctrl;
   unsigned long long bt = 0;
-  if (tid == 0) s_abort = 0;
-
-  Ctx x;
-  x.rc = a.rc;
-  {
-    // smallest warp groups (>= 32 threads) whose row blocks cover rc rows in one pass
-    constexpr int RBk = rows_per_tile(KIND);
-    int gt = kBlock / 4;
-    while (gt > 32 && (kBlock / gt) * RBk < a.rc) gt >>= 1;
-    x.gt = gt;
-  }
-  x.rb = (int)(((long long)b * N) / G);
-  x.nr = (int)(((long long)(b + 1) * N) / G) - x.rb;
-  x.slab = a.slab_bytes > 0 ? dyn : nullptr;
-  x.S = (double*)(dyn + a.slab_bytes);
-  x.spar = x.S + 6 * d * x.rc;
-  x.sth = x.spar + x.rc;
-  x.srs = x.sth + x.rc;
-  x.sscale = (float*)(x.srs + x.rc);
-  x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
-  x.rtol = a.rtol;
-  x.thr = a.atol / a.rtol;
-  x.m0 = 0.0; x.m1 = 0.0;
-  x.c21 = x.c32 = x.hs = x.h0s = 0.0;
-  x.single = (a.job == JOB_RHS) ? (a.rhs_f == 0 && a.rhs_s == 0 && a.rhs_g == 0) : (a.variant == V_SINGLE);
   const bool single = x.single;
-
-  // this CTA's weight rows into shared memory (contiguous in the [N][ld] layout)
-  if (a.slab_bytes > 0) {
-    const size_t eb = (size_t)KLoad<ST>::BYTES;
-    const uint4* src = reinterpret_cast<const uint4*>((const char*)a.q + (size_t)x.rb * a.ld * eb);
-    uint4* dst = reinterpret_cast<uint4*>(dyn);
-    const int n16 = (int)((size_t)x.nr * a.ld * eb / 16);
-    for (int e = tid; e < n16; e += blockDim.x) dst[e] = ld_stream16(src + e);
-  }
-  float* smlp = a.mlp ? (float*)(dyn + a.smem_mlp_off) : nullptr;
-  if (a.mlp)
-    for (int k = tid; k < kMlpModel; k += blockDim.x) smlp[k] = a.mlp[k];
-  // per-agent parameters and the initial state of this CTA's agents
-  for (int li = tid; li < x.nr; li += blockDim.x) {
-    const int i = x.rb + li;
-    x.spar[li] = a.par[i];
-    x.sth[li] = a.theta_h ? a.theta_h[i] : 0.0;
-    x.srs[li] = a.rowsum[i];
-    x.sscale[li] = a.scale[i];
-#pragma unroll
-    for (int c = 0; c < d; ++c) {
-      const double y = a.X[c * N + i];
-      if (a.job == JOB_SOLVE)
-        for (long long k = 0; k < a.n_out && a.t_out[k] <= a.t0; ++k) a.y_out[(size_t)k * d * N + c * N + i] = y;
-      sv<KIND>(x, x.iX, c, li) = single ? (double)(float)y : y;
-      if (a.job == JOB_ATTEMPT) {
-        const double k1 = a.Kb[0][c * N + i];
-        sv<KIND>(x, x.iK1, c, li) = single ? (double)(float)k1 : k1;
-      }
-    }
-  }
-  __syncthreads();
-
-  // -------------------------------------------------------------------- RHS
+  (void)b;
   if (a.job == JOB_RHS) {
     x.p = Prec{a.rhs_f, a.rhs_s, a.rhs_g};
     for (int li = tid; li < x.nr; li += blockDim.x) {
@@ -696,7 +658,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
       for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
       put_jv<KIND>(a, 0, x.rb + li, Y, x.p.g, single);
     }
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) return;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) return;
     stage<KIND, ST>(a, x, PH_RHS, 0, s_grp);
     return;
   }
@@ -723,7 +685,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
       put_jv<KIND>(a, 0, x.rb + li, Y, p4.g, single);
     }
   }
-  if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
+  if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
 
   if (a.job == JOB_SOLVE) {
     // ---- K1 = f(t0, y0) with the k4 row; starting-step norms d0, d1
@@ -732,7 +694,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     stage<KIND, ST>(a, x, PH_K1, 0, s_grp);
     block_max(x.m0, &ctrl->red[0], s_red);
     block_max(x.m1, &ctrl->red[1], s_red);
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
     if (tid == 0) {
       sc.n_rhs = 1;
       const double d0 = ld_bits(&ctrl->red[0]);
@@ -753,11 +715,11 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
           Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.h0s, sv<KIND>(x, x.iK1, c, li), single);
         put_jv<KIND>(a, 1, x.rb + li, Y, p4.g, single);
       }
-      if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
+      if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       x.m0 = 0.0;
       stage<KIND, ST>(a, x, PH_F1, 1, s_grp);
       block_max(x.m0, &ctrl->red[2], s_red);
-      if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) goto finish_up;
+      if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       if (tid == 0) {
         sc.n_rhs = 2;
         const double h0 = sc.hs;
@@ -798,7 +760,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     }
     __syncthreads();
     if (sc.stop) break;
-    const bool rec = (a.hist != nullptr) && b == 0 && tid == 0 && (sc.n_acc + sc.n_rej) < a.hist_cap;
+    const bool rec = (a.hist != nullptr) && leader && (sc.n_acc + sc.n_rej) < a.hist_cap;
     unsigned long long ts[5];
     if (rec) ts[0] = globaltimer_ns();
     x.hs = sc.hs;
@@ -812,21 +774,21 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
         Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
       put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
     }
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[1] = globaltimer_ns();
     // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
-    if (b == 0 && tid == 0) ctrl->emax[parity ^ 1] = 0ull;
+    if (leader) ctrl->emax[parity ^ 1] = 0ull;
     x.p = p2; x.pn = p3;
     stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[2] = globaltimer_ns();
     // ---- B3: K3 = f(Y3); X' -> j-vector 2
     x.p = p3; x.pn = p4;
     stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[3] = globaltimer_ns();
     // ---- B4: K4 = f(X'); error norm
-    if (b == 0 && tid == 0) {
+    if (leader) {
       ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
       if (a.progress) *a.progress = sc.t;
     }
@@ -834,7 +796,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
     x.m1 = 0.0;
     stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
     block_max(x.m1, &ctrl->emax[parity], s_red);
-    if (!grid_sync(ctrl, bt, a.spin_limit, &s_abort)) break;
+    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
     // ---- decision (thread 0; warp 0 runs the learned proposer when installed)
     if (tid == 0) {
       const double E = ld_bits(&ctrl->emax[parity]);
@@ -951,13 +913,13 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
 
 finish_up:
   __syncthreads();
-  if (a.job == JOB_SOLVE && a.final_y != nullptr && !s_abort) {
+  if (a.job == JOB_SOLVE && a.final_y != nullptr && !*s_abort) {
     for (int li = tid; li < x.nr; li += blockDim.x) {
 #pragma unroll
       for (int c = 0; c < d; ++c) a.final_y[c * N + x.rb + li] = sv<KIND>(x, x.iX, c, li);
     }
   }
-  if (b == 0 && tid == 0) {
+  if (leader) {
     if (sc.status != S_OK) atomicCAS(&ctrl->status, 0, sc.status);
     ctrl->n_acc = sc.n_acc;
     ctrl->n_rej = sc.n_rej;
@@ -965,6 +927,175 @@ finish_up:
     ctrl->n_out = sc.next_out;
     ctrl->t = sc.t;
     ctrl->h = sc.h;
+  }
+}
+
+template <int KIND, int ST>
+__global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
+  constexpr int d = Dim<KIND>::d;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ int s_abort;
+  __shared__ unsigned long long s_red[kBlock / 32];
+  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
+  __shared__ Scal sc;
+  const int N = a.N;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_abort = 0;
+
+  Ctx x;
+  x.rc = a.rc;
+  x.gt = group_threads<KIND>(a.rc);
+  x.rb = (int)(((long long)b * N) / G);
+  x.nr = (int)(((long long)(b + 1) * N) / G) - x.rb;
+  x.slab = a.slab_bytes > 0 ? dyn : nullptr;
+  x.S = (double*)(dyn + a.slab_bytes);
+  x.spar = x.S + 6 * d * x.rc;
+  x.sth = x.spar + x.rc;
+  x.srs = x.sth + x.rc;
+  x.sscale = (float*)(x.srs + x.rc);
+  x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
+  x.rtol = a.rtol;
+  x.thr = a.atol / a.rtol;
+  x.m0 = 0.0; x.m1 = 0.0;
+  x.c21 = x.c32 = x.hs = x.h0s = 0.0;
+  x.single = (a.job == JOB_RHS) ? (a.rhs_f == 0 && a.rhs_s == 0 && a.rhs_g == 0) : (a.variant == V_SINGLE);
+  const bool single = x.single;
+
+  // this CTA's weight rows into shared memory (contiguous in the [N][ld] layout)
+  if (a.slab_bytes > 0) {
+    const size_t eb = (size_t)KLoad<ST>::BYTES;
+    const uint4* src = reinterpret_cast<const uint4*>((const char*)a.q + (size_t)x.rb * a.ld * eb);
+    uint4* dst = reinterpret_cast<uint4*>(dyn);
+    const int n16 = (int)((size_t)x.nr * a.ld * eb / 16);
+    for (int e = tid; e < n16; e += blockDim.x) dst[e] = ld_stream16(src + e);
+  }
+  float* smlp = a.mlp ? (float*)(dyn + a.smem_mlp_off) : nullptr;
+  if (a.mlp)
+    for (int k = tid; k < kMlpModel; k += blockDim.x) smlp[k] = a.mlp[k];
+  // per-agent parameters and the initial state of this CTA's agents
+  for (int li = tid; li < x.nr; li += blockDim.x) {
+    const int i = x.rb + li;
+    x.spar[li] = a.par[i];
+    x.sth[li] = a.theta_h ? a.theta_h[i] : 0.0;
+    x.srs[li] = a.rowsum[i];
+    x.sscale[li] = a.scale[i];
+#pragma unroll
+    for (int c = 0; c < d; ++c) {
+      const double y = a.X[c * N + i];
+      if (a.job == JOB_SOLVE)
+        for (long long k = 0; k < a.n_out && a.t_out[k] <= a.t0; ++k) a.y_out[(size_t)k * d * N + c * N + i] = y;
+      sv<KIND>(x, x.iX, c, li) = single ? (double)(float)y : y;
+      if (a.job == JOB_ATTEMPT) {
+        const double k1 = a.Kb[0][c * N + i];
+        sv<KIND>(x, x.iK1, c, li) = single ? (double)(float)k1 : k1;
+      }
+    }
+  }
+  __syncthreads();
+
+  run_job<KIND, ST, false>(a, x, sc, &s_abort, s_red, s_grp, smlp);
+}
+
+}  // namespace bs3
+
+namespace bs3 {
+
+// ---------------------------------------------------------------------------
+// Ragged batches of independent systems: each CTA takes whole systems from a
+// work queue (largest first) and solves them alone, with CTA barriers only;
+// the state lives in global memory (slots [6][d][N] per system).
+// ---------------------------------------------------------------------------
+struct SysDesc {
+  int N, ld;
+  const void* q;
+  const float* scale;
+  const double* rowsum;
+  const double* par;
+  const double* theta_h;
+  const double* y0;
+  double* y_final;
+  double* state;     // [6][d][N]
+  float* jv32;       // [3][2][ld]
+  double* jv64;      // [3][2][ld]
+  Control* ctrl;
+  double t0, t1;
+};
+
+struct BatchArgs {
+  Args common;       // variant, Sigma mode, tolerances, limits
+  const SysDesc* sys;
+  int S;
+  int* next;         // work-queue counter (zero before the launch)
+};
+
+template <int KIND, int ST>
+__global__ void __launch_bounds__(kBlock, 1) bs3_batch_kernel(BatchArgs ba) {
+  constexpr int d = Dim<KIND>::d;
+  __shared__ int s_abort, s_sys;
+  __shared__ unsigned long long s_red[kBlock / 32];
+  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
+  __shared__ Scal sc;
+  const int tid = threadIdx.x;
+  while (true) {
+    __syncthreads();
+    if (tid == 0) {
+      s_sys = atomicAdd(ba.next, 1);
+      s_abort = 0;
+    }
+    __syncthreads();
+    const int sidx = s_sys;
+    if (sidx >= ba.S) break;
+    const SysDesc D = ba.sys[sidx];
+    Args a = ba.common;
+    a.job = JOB_SOLVE;
+    a.N = D.N;
+    a.ld = D.ld;
+    a.q = D.q;
+    a.scale = D.scale;
+    a.rowsum = D.rowsum;
+    a.par = D.par;
+    a.theta_h = D.theta_h;
+    a.X = const_cast<double*>(D.y0);
+    a.jv32 = D.jv32;
+    a.jv64 = D.jv64;
+    a.ctrl = D.ctrl;
+    a.final_y = D.y_final;
+    a.t0 = D.t0;
+    a.t1 = D.t1;
+    a.hmax = 0.1 * (D.t1 - D.t0);
+    a.n_out = 0;
+    a.rc = D.N;
+    a.slab_bytes = 0;
+    a.hist = nullptr;
+    a.mlp = nullptr;
+    a.cancel = nullptr;
+    a.progress = nullptr;
+    Ctx x;
+    x.rc = D.N;
+    x.gt = group_threads<KIND>(D.N);
+    x.rb = 0;
+    x.nr = D.N;
+    x.slab = nullptr;
+    x.S = D.state;
+    x.spar = const_cast<double*>(D.par);
+    x.srs = const_cast<double*>(D.rowsum);
+    x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum);   // read only by the circadian kind
+    x.sscale = const_cast<float*>(D.scale);
+    x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
+    x.rtol = a.rtol;
+    x.thr = a.atol / a.rtol;
+    x.m0 = 0.0; x.m1 = 0.0;
+    x.c21 = x.c32 = x.hs = x.h0s = 0.0;
+    x.single = (a.variant == V_SINGLE);
+    for (int li = tid; li < D.N; li += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < d; ++c) {
+        const double y = D.y0[c * D.N + li];
+        sv<KIND>(x, x.iX, c, li) = x.single ? (double)(float)y : y;
+      }
+    __syncthreads();
+    run_job<KIND, ST, true>(a, x, sc, &s_abort, s_red, s_grp, nullptr);
   }
 }
 

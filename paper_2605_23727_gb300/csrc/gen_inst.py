@@ -11,10 +11,12 @@ STORES = [("f64", "ST_F64"), ("f32", "ST_F32"), ("bf16", "ST_BF16"), ("f16", "ST
 for kname, kenum in KINDS:
     for sname, senum in STORES:
         with open(os.path.join(HERE, f"inst_{kname}_{sname}.cu"), "w") as fh:
-            fh.write(f"// Generated by gen_inst.py: solver kernel for {kname} with {sname} weights.\n"
+            fh.write(f"// Generated by gen_inst.py: solver kernels for {kname} with {sname} weights.\n"
                      f'#include "bs3_solver.cuh"\n\n'
                      f"namespace bs3 {{\n"
                      f"const void* kernel_{kname}_{sname}() {{ return (const void*)bs3_kernel<{kenum}, {senum}>; }}\n"
+                     f"const void* batch_kernel_{kname}_{sname}() {{\n"
+                     f"  return (const void*)bs3_batch_kernel<{kenum}, {senum}>;\n}}\n"
                      f"}}  // namespace bs3\n")
 
 with open(os.path.join(HERE, "bs3_kernels.h"), "w") as fh:
@@ -23,8 +25,14 @@ with open(os.path.join(HERE, "bs3_kernels.h"), "w") as fh:
     for kname, _ in KINDS:
         for sname, _ in STORES:
             fh.write(f"const void* kernel_{kname}_{sname}();\n")
+            fh.write(f"const void* batch_kernel_{kname}_{sname}();\n")
     fh.write("\ninline const void* kernel_lookup(int kind, int store) {\n"
              "  static const void* (*const table[4][5])() = {\n")
     for kname, _ in KINDS:
         fh.write("      {" + ", ".join(f"kernel_{kname}_{s}" for s, _ in STORES) + "},\n")
+    fh.write("  };\n  return table[kind][store]();\n}\n\n")
+    fh.write("inline const void* batch_kernel_lookup(int kind, int store) {\n"
+             "  static const void* (*const table[4][5])() = {\n")
+    for kname, _ in KINDS:
+        fh.write("      {" + ", ".join(f"batch_kernel_{kname}_{s}" for s, _ in STORES) + "},\n")
     fh.write("  };\n  return table[kind][store]();\n}\n}  // namespace bs3\n")

@@ -1,6 +1,9 @@
-// Generated by gen_inst.py: solver kernel for circadian with bf16 weights.
+// Generated by gen_inst.py: solver kernels for circadian with bf16 weights.
 #include "bs3_solver.cuh"
 
 namespace bs3 {
 const void* kernel_circadian_bf16() { return (const void*)bs3_kernel<K_CIRCADIAN, ST_BF16>; }
+const void* batch_kernel_circadian_bf16() {
+  return (const void*)bs3_batch_kernel<K_CIRCADIAN, ST_BF16>;
+}
 }  // namespace bs3

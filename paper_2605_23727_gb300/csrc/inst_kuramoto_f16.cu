@@ -1,6 +1,9 @@
-// Generated by gen_inst.py: solver kernel for kuramoto with f16 weights.
+// Generated by gen_inst.py: solver kernels for kuramoto with f16 weights.
 #include "bs3_solver.cuh"
 
 namespace bs3 {
 const void* kernel_kuramoto_f16() { return (const void*)bs3_kernel<K_KURAMOTO, ST_F16>; }
+const void* batch_kernel_kuramoto_f16() {
+  return (const void*)bs3_batch_kernel<K_KURAMOTO, ST_F16>;
+}
 }  // namespace bs3

@@ -1,6 +1,9 @@
-// Generated by gen_inst.py: solver kernel for lco_paper with f16 weights.
+// Generated by gen_inst.py: solver kernels for lco_paper with f16 weights.
 #include "bs3_solver.cuh"
 
 namespace bs3 {
 const void* kernel_lco_paper_f16() { return (const void*)bs3_kernel<K_LCO_PAPER, ST_F16>; }
+const void* batch_kernel_lco_paper_f16() {
+  return (const void*)bs3_batch_kernel<K_LCO_PAPER, ST_F16>;
+}
 }  // namespace bs3
