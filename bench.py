@@ -61,6 +61,9 @@ CASES = {
     "circadian16384_mixed1_bf16": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "bf16"),
     "ensemble256_kuramoto8192": None,
     "ensemble128_kuramoto1024": None,
+    "ragged1000_lco_mixed1_f16": None,
+    "proposer_lco32768_f16": None,
+    "proposer_lco8192_f16": None,
 }
 
 
@@ -95,9 +98,88 @@ def run_ensemble_case(name):
         sys.exit(1)
 
 
+def run_ragged_case(name):
+    """1000 independent second-order oscillator systems, N log-uniform in
+    [64, 4096], f16 weights, Mixed1, rtol 1e-6, t in [0, 10], one launch."""
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    count = 1000
+    systems = workloads.lco_ragged_batch(count=count, n_min=64, n_max=4096, seed=0, t1=10.0, rtol=RTOL)
+    Ns = [w.N for w in systems]
+    K = np.concatenate([np.asarray(w.coupling, dtype=np.float32).ravel() for w in systems])
+    params = np.concatenate([w.params for w in systems])
+    y0 = np.concatenate([w.y0 for w in systems])
+    t0 = np.zeros(count)
+    t1 = np.full(count, 10.0)
+    rc, yf, stats, kms = bs3.bs3_batch_solve(bs3.LCO_CFG, Ns, params, K, bs3.F16, y0, t0, t1, RTOL, RTOL,
+                                             bs3.MIXED1, bs3.ACC_FLOAT2)
+    evals = np.array([st.n_rhs_evals for st in stats], dtype=np.float64)
+    nn = np.array(Ns, dtype=np.float64)
+    weight_bytes = float(np.sum(evals * nn * nn * 2))
+    print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "systems": count,
+                      "sum_N2": float(np.sum(nn * nn)), "kernel_ms": kms,
+                      "attempts_total": int(sum(st.n_accepted + st.n_rejected for st in stats)),
+                      "weight_GBs": weight_bytes / (kms * 1e-3) / 1e9, "all_ok": all(st.status == 0 for st in stats)}))
+    if rc != bs3.OK:
+        sys.exit(1)
+
+
+def run_proposer_case(name):
+    """Second-order oscillators N = 32768, f16 weights, Mixed1, rtol 1e-6,
+    t in [0, 10], with and without the learned step-size proposer (trained on
+    step histories of the three smaller workloads, other seeds)."""
+    import torch
+    from paper_2605_23727_gb300 import bs3, proposer
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    train = []
+    for seed in (101, 102, 103):
+        for rtol in (1e-4, 1e-5, 1e-6, 1e-7):
+            train.append((workloads.lco_config(256, seed), "f64", "double", rtol))
+    train.append((workloads.kuramoto(1024, 101, t1=50.0), "f32", "mixed2", 1e-6))
+    train.append((workloads.circadian(256, 101, t1=240.0), "f32", "mixed2", 1e-6))
+    X, y = proposer.dataset(train)
+    model, loss = proposer.train(X, y, epochs=120, batch=256, lr=2e-3)
+    N = 32768 if name == "proposer_lco32768_f16" else 8192
+    w = workloads.lco_config(N, 7, t1=10.0, dtype=np.float32)
+    s = bs3.System.from_workload(w, "f16")
+    y0 = torch.tensor(w.y0, device="cuda")
+
+    def run(rtol, variant):
+        yo = torch.empty_like(y0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, rtol, rtol, bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2,
+                               None, 0, None, yo, 0)
+        e1.record()
+        e1.synchronize()
+        assert rc == bs3.OK, bs3.bs3_status_string(rc)
+        return yo.cpu().numpy(), st, e0.elapsed_time(e1)
+
+    y_ref, _, _ = run(1e-9, "mixed2")     # same f16 weights, tight tolerance
+    y_plain, st_plain, ms_plain = run(RTOL, "mixed1")
+    assert bs3.bs3_set_proposer(s.handle, model) == bs3.OK
+    run(RTOL, "mixed1")
+    y_learn, st_learn, ms_learn = run(RTOL, "mixed1")
+    s.close()
+    out = {"case": name, "N": N, "training_samples": int(len(y)), "final_train_loss": float(loss[-1])}
+    for tag, yv, st, ms in (("plain", y_plain, st_plain, ms_plain), ("learned", y_learn, st_learn, ms_learn)):
+        out[tag] = {"accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals, "ms": ms,
+                    "global_error_vs_tight": normalized_error(y_ref, yv, N)}
+    print(json.dumps(out))
+
+
 def run_case(name):
     if name.startswith("ensemble"):
         return run_ensemble_case(name)
+    if name.startswith("ragged"):
+        return run_ragged_case(name)
+    if name.startswith("proposer"):
+        return run_proposer_case(name)
     import torch
     from paper_2605_23727_gb300 import bs3
     import __graft_entry__
@@ -311,6 +393,9 @@ def run_gpu(args):
           if k.startswith("mixed") and v["global_error"] <= ERROR_FACTOR * e_double]
     head = min(ok)[1] if ok else "mixed2/f32"
     h_variant, h_store = head.split("/")
+    from paper_2605_23727_gb300 import autotune
+    plan, plan_us = autotune.tuned(system(h_store), y0_d, w.t0, w.t1, RTOL, h_variant, args.accum,
+                                   torch.cuda.get_device_name(dev))
 
     # ---------------------------------------------------------------- timed
     for _ in range(args.warmup):
@@ -383,6 +468,7 @@ def run_gpu(args):
         "data": "synthetic (seeded numpy; Kuramoto shaped like the paper's Benchmark 2)",
         "config": {"workload": WORKLOAD, "N": w.N, "t1": T1, "rtol": RTOL, "atol": RTOL,
                    "variant": h_variant, "weights": h_store, "sigma_d_sum": args.accum,
+                   "launch_plan": {"resident_weights": plan[0], "ctas": plan[1]},
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "l2": "flushed between steps (512 MiB write, then 512 MiB read of another buffer, "
                          "outside the timed events)",

@@ -173,13 +173,24 @@ enum {
      * stream them from HBM/L2 at every stage.  Results are identical.  On
      * GB300 keeping them on chip leaves too little L1 for the j-vectors and
      * measured slower (Kuramoto N=4096, bf16: 64.5 vs 61.7 ms). */
-    BS3_TUNE_RESIDENT_WEIGHTS = 1
+    BS3_TUNE_RESIDENT_WEIGHTS = 1,
+    /* CTAs of the persistent launch: 0 (default) = one per SM; otherwise at
+     * most this many (fewer CTAs = cheaper grid barriers, more rows each). */
+    BS3_TUNE_CTAS = 2
 };
 
 /* Sets a tuning knob of the system (takes effect at the next launch).
  * Errors: BS3_ERR_INVALID_ARG for an unknown key or value.  The paper has no
  * counterpart (it concerns only how this library maps the method on the GPU). */
 int bs3_set_tuning(bs3_system_t sys, int key, int64_t value);
+
+/* Autotuner: times bounded solves (at most `attempts` attempts each, from y0
+ * on the device) of every candidate launch plan -- resident weights off/on x
+ * CTAs = SMs, SMs/2, SMs/4 -- and applies the fastest per attempt to the
+ * system.  choice_out[2] (host) receives (resident, ctas), us_out (host) the
+ * chosen plan's microseconds per attempt.  The paper has no counterpart. */
+int bs3_autotune(bs3_system_t sys, const double* y0, double t0, double t1, double rtol, int variant, int accum,
+                 int attempts, int64_t* choice_out, double* us_out);
 
 /* Step history (tracing, and the training data of a learned step-size
  * proposer): with capacity > 0, each later bs3_solve records its first
@@ -274,12 +285,13 @@ int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega
  *   BS3_CIRCADIAN N_k values then the 8 constants, which must agree across the
  *   batch; NULL for BS3_LCO_PAPER); K: each system's N_k x N_k binary32
  *   row-major weights; y0, y_final: each system's d*N_k state (SoA);
- *   t0[S], t1[S]; stats[S] (may be NULL).
+ *   t0[S], t1[S]; stats[S] (may be NULL); *kernel_ms (may be NULL) receives
+ *   the device time of the solve launch alone (without quantisation and copies).
  * store, rtol, atol, variant, accum as bs3_set_coupling / bs3_solve (wall-clock
  * limits not enforced).  Returns the first non-OK system status, else BS3_OK. */
 int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params, const float* K, int store,
                     const double* y0, const double* t0, const double* t1, double rtol, double atol, int variant,
-                    int accum, double* y_final, bs3_stats* stats, int device, void* stream);
+                    int accum, double* y_final, bs3_stats* stats, double* kernel_ms, int device, void* stream);
 
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384

@@ -37,8 +37,9 @@ EXPORTED = (
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
-    "bs3_ensemble_solve", "bs3_batch_solve",
+    "bs3_ensemble_solve", "bs3_batch_solve", "bs3_autotune",
 )
+TUNE_CTAS = 2
 MLP_PARAMS = 1313
 MLP_MODEL = 1325
 NOALLOC_MAX_N = 16384
@@ -101,7 +102,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_set_proposer": (I, [P, P]),
         "bs3_tc_gemm": (I, [I64, I64, I64, P, P, P]),
         "bs3_ensemble_solve": (I, [P, I64, I64, P, P, D, D, D, D, P, P, P, P, ctypes.POINTER(I64), P]),
-        "bs3_batch_solve": (I, [I, I64, P, P, P, I, P, P, P, D, D, I, I, P, P, I, P]),
+        "bs3_batch_solve": (I, [I, I64, P, P, P, I, P, P, P, D, D, I, I, P, P, ctypes.POINTER(D), I, P]),
+        "bs3_autotune": (I, [P, P, D, D, D, I, I, I, P, ctypes.POINTER(D)]),
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
@@ -262,7 +264,7 @@ def bs3_ensemble_solve(K, N: int, T: int, omega, theta0, t0: float, t1: float, r
 
 def bs3_batch_solve(kind: int, Ns, params, K, store: int, y0, t0, t1, rtol: float, atol: float, variant: int,
                     accum: int, device: int = 0, stream: int = 0):
-    """Host arrays in, returns (rc, y_final concat, stats list)."""
+    """Host arrays in, returns (rc, y_final concat, stats list, kernel ms)."""
     Ns = np.ascontiguousarray(Ns, dtype=np.int64)
     S = Ns.size
     p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
@@ -272,9 +274,19 @@ def bs3_batch_solve(kind: int, Ns, params, K, store: int, y0, t0, t1, rtol: floa
     t1 = np.ascontiguousarray(t1, dtype=np.float64)
     yf = np.zeros_like(y0)
     stats = (bs3_stats * S)()
+    kms = ctypes.c_double()
     rc = load().bs3_batch_solve(kind, S, _ptr(Ns), _ptr(p), _ptr(K), store, _ptr(y0), _ptr(t0), _ptr(t1), rtol, atol,
-                                variant, accum, _ptr(yf), ctypes.cast(stats, ctypes.c_void_p), device, stream or None)
-    return rc, yf, list(stats)
+                                variant, accum, _ptr(yf), ctypes.cast(stats, ctypes.c_void_p), ctypes.byref(kms),
+                                device, stream or None)
+    return rc, yf, list(stats), kms.value
+
+
+def bs3_autotune(sys_: int, y0, t0: float, t1: float, rtol: float, variant: int, accum: int, attempts: int):
+    """Returns (rc, (resident, ctas), microseconds per attempt)."""
+    choice = np.zeros(2, dtype=np.int64)
+    us = ctypes.c_double()
+    rc = load().bs3_autotune(sys_, _ptr(y0), t0, t1, rtol, variant, accum, attempts, _ptr(choice), ctypes.byref(us))
+    return rc, (int(choice[0]), int(choice[1])), us.value
 
 
 def bs3_destroy_system(sys_: int) -> int:

@@ -63,6 +63,7 @@ struct bs3_system {
   int slab = 0;
   bool allow_resident = false;   // see BS3_TUNE_RESIDENT_WEIGHTS
   int l2_keep = 1;
+  int tune_ctas = 0;           // 0 = one CTA per SM
   float* mlp = nullptr;        // learned proposer (kMlpModel binary32, weights bf16-rounded)
   bool mlp_on = false;
   int mlp_off = 0;
@@ -221,7 +222,8 @@ int pick_grid(bs3_system* s) {
   int sms = 0;
   BS3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
   const int rb = rows_per_tile(s->kind);
-  const int64_t grid = std::min<int64_t>(sms, std::max<int64_t>(1, (s->N + rb - 1) / rb));
+  const int64_t cap = s->tune_ctas > 0 ? std::min(s->tune_ctas, sms) : sms;
+  const int64_t grid = std::min<int64_t>(cap, std::max<int64_t>(1, (s->N + rb - 1) / rb));
   const int rc = (int)((s->N + grid - 1) / grid);
   const size_t state = (state_smem_bytes(s->d, rc) + 15) / 16 * 16;
   const size_t mlp = s->mlp_on ? (size_t)kMlpModel * sizeof(float) : 0;
@@ -402,7 +404,7 @@ int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_param
 
 int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params, const float* K, int store,
                     const double* y0, const double* t0, const double* t1, double rtol, double atol, int variant,
-                    int accum, double* y_final, bs3_stats* stats, int device, void* stream_) {
+                    int accum, double* y_final, bs3_stats* stats, double* kernel_ms, int device, void* stream_) {
   if (kind < BS3_LCO_CFG || kind > BS3_CIRCADIAN || S < 1 || S > (1 << 24) || !Ns || !K || !y0 || !t0 || !t1 ||
       !y_final)
     return BS3_ERR_INVALID_ARG;
@@ -539,8 +541,19 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
     const unsigned grid = (unsigned)std::min<int64_t>(sms, S);
     void* kargs[] = {&ba};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (kernel_ms && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess ||
+                      cudaEventRecord(ev0, st) != cudaSuccess)) { rc = BS3_ERR_CUDA; break; }
     if (cudaLaunchKernel(batch_kernel_lookup(kind, store), dim3(grid), dim3(kBlock), kargs, 0, st) != cudaSuccess) {
       rc = BS3_ERR_CUDA; break;
+    }
+    if (kernel_ms) {
+      float ms = 0.f;
+      if (cudaEventRecord(ev1, st) != cudaSuccess || cudaEventSynchronize(ev1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      *kernel_ms = ms;
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
     }
     if (cudaMemcpyAsync(y_final, arena + oYF, (size_t)d * TN * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(ctl.data(), arena + oCtl, S * sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -602,7 +615,73 @@ int bs3_set_tuning(bs3_system_t s, int key, int64_t value) {
     s->grid_store = -1;   // re-plan the launch
     return BS3_OK;
   }
+  if (key == BS3_TUNE_CTAS) {
+    if (value < 0 || value > 65536) return BS3_ERR_INVALID_ARG;
+    s->tune_ctas = (int)value;
+    s->grid_store = -1;
+    return BS3_OK;
+  }
   return BS3_ERR_INVALID_ARG;
+}
+
+int bs3_autotune(bs3_system_t s, const double* y0, double t0, double t1, double rtol, int variant, int accum,
+                 int attempts, int64_t* choice_out, double* us_out) {
+  if (!s || !y0 || attempts < 4 || s->store < 0) return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(s->device);
+  int sms = 0;
+  BS3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+  const bool res0 = s->allow_resident;
+  const int ctas0 = s->tune_ctas;
+  double best = 1e300;
+  int best_res = res0 ? 1 : 0, best_ctas = ctas0;
+  bs3_limits lim;
+  bs3_default_limits(&lim);
+  lim.max_attempts = attempts;
+  cudaEvent_t e0, e1;
+  BS3_CUDA(cudaEventCreate(&e0));
+  BS3_CUDA(cudaEventCreate(&e1));
+  const int cand_ctas[3] = {sms, sms / 2, sms / 4};
+  int rc = BS3_OK;
+  for (int res = 0; res <= 1 && rc == BS3_OK; ++res) {
+    for (int c = 0; c < 3 && rc == BS3_OK; ++c) {
+      s->allow_resident = res != 0;
+      s->tune_ctas = cand_ctas[c] > 0 ? cand_ctas[c] : 1;
+      s->grid_store = -1;
+      if (pick_grid(s) != BS3_OK) continue;
+      if (res && s->slab == 0) continue;   // resident plan does not fit: same as streamed
+      bs3_stats st;
+      for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+        if (cudaEventRecord(e0, s->stream) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+        const int r = bs3_solve(s, t0, t1, y0, rtol, rtol, variant, accum, nullptr, 0, nullptr, nullptr, 0, &st, &lim);
+        if (r != BS3_OK && r != BS3_ERR_MAX_STEPS) { rc = r; break; }
+        if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = BS3_ERR_CUDA;
+          break;
+        }
+      }
+      if (rc != BS3_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double us = 1000.0 * ms / (double)std::max<int64_t>(1, st.n_accepted + st.n_rejected);
+      if (us < best) {
+        best = us;
+        best_res = res;
+        best_ctas = s->tune_ctas;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->allow_resident = rc == BS3_OK ? best_res != 0 : res0;
+  s->tune_ctas = rc == BS3_OK ? best_ctas : ctas0;
+  s->grid_store = -1;
+  if (rc != BS3_OK) return rc;
+  if (choice_out) {
+    choice_out[0] = best_res;
+    choice_out[1] = best_ctas;
+  }
+  if (us_out) *us_out = best;
+  return BS3_OK;
 }
 
 int bs3_set_history(bs3_system_t s, int64_t capacity) {

@@ -21,7 +21,7 @@ def _batch(systems, store, variant, kind="lco_cfg"):
     y0 = np.concatenate([w.y0 for w in systems])
     t0 = np.array([w.t0 for w in systems])
     t1 = np.array([w.t1 for w in systems])
-    rc, yf, stats = bs3.bs3_batch_solve(bs3.KIND_IDS[kind], Ns, params, K, bs3.DTYPE_IDS[store], y0, t0, t1,
+    rc, yf, stats, _ = bs3.bs3_batch_solve(bs3.KIND_IDS[kind], Ns, params, K, bs3.DTYPE_IDS[store], y0, t0, t1,
                                         systems[0].rtol, systems[0].atol, bs3.VARIANT_IDS[variant],
                                         bs3.ACC_FLOAT2)
     assert rc == bs3.OK, bs3.bs3_status_string(rc)
@@ -56,3 +56,23 @@ def test_ragged_kuramoto_and_single_system_entry_agree():
         assert rc == bs3.OK
         assert abs((st.n_accepted + st.n_rejected) - (stats[k].n_accepted + stats[k].n_rejected)) <= 2
         assert metrics.normalized_final_error(y, out[k], w.N) < 1e-6
+
+
+def test_autotuner_picks_a_valid_plan_and_keeps_results():
+    bs3 = library()
+    torch = torch_cuda()
+    w = W.kuramoto(2048, 8, t1=2.0)
+    s = bs3.System.from_workload(w, "bf16")
+    y0 = torch.tensor(w.y0, device="cuda")
+    rc, y_default, st_default = None, None, None
+    rc, st_default = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, 1e-6, 1e-6, bs3.MIXED1, bs3.ACC_FLOAT2, None, 0, None,
+                                   yd := torch.empty_like(y0), 0)
+    assert rc == bs3.OK
+    rc, plan, us = bs3.bs3_autotune(s.handle, y0, w.t0, w.t1, 1e-6, bs3.MIXED1, bs3.ACC_FLOAT2, 20)
+    assert rc == bs3.OK and plan[0] in (0, 1) and plan[1] >= 1 and us > 0
+    yt = torch.empty_like(y0)
+    rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, 1e-6, 1e-6, bs3.MIXED1, bs3.ACC_FLOAT2, None, 0, None, yt, 0)
+    s.close()
+    assert rc == bs3.OK
+    assert abs((st.n_accepted + st.n_rejected) - (st_default.n_accepted + st_default.n_rejected)) <= 2
+    assert metrics.normalized_final_error(yd.cpu().numpy(), yt.cpu().numpy(), w.N) < 1e-6
