@@ -88,6 +88,21 @@ __device__ __forceinline__ uint4 ld_stream16_pol(const void* p, unsigned long lo
   return r;
 }
 
+// q^(1/3) for the step-size controller, q > 0.  A dependent binary64 op
+// costs ~30 ns on GB300 and pow() ~3 us, all on the serial path of every
+// attempt; instead: the binary32 cube root (relative error ~1e-7), then one
+// Newton step y - (y^3 - q) / (3 y^2) in binary64 with a binary32 estimate of
+// 1 / (3 y^2), which leaves a relative error of ~1e-14.  q is clamped to
+// [1e-30, 1e30]; beyond [0.24, 245] the controller's limits (factor in
+// [0.5, 5] with safety factor 0.8) decide the step anyway.
+__device__ __forceinline__ double cbrt_pos(double q) {
+  q = fmin(fmax(q, 1e-30), 1e30);
+  const float yf = cbrtf((float)q);
+  const double y = (double)yf;
+  const double r = (double)(1.0f / (3.0f * yf * yf));
+  return fma(-fma(y * y, y, -q), r, y);
+}
+
 // Grid barrier for a cooperative launch.  Every CTA adds one arrival to a
 // monotonic counter (release) and polls it until it reaches its target.  The
 // wait is bounded by spin_limit polls; a CTA that gives up sets the status to

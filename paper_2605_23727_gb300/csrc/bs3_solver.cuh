@@ -825,7 +825,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
           ++e;
         }
         sc.out_end = e;
-        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * pow(rtol / E, 1.0 / 3.0));
+        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * cbrt_pos(rtol / E));
         if (sc.rejected) fac = fmin(1.0, fac);
         sc.h = h * fac;
         sc.t = t_new;
@@ -847,7 +847,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         sc.accepted = 1;
       } else {
         ++sc.n_rej;
-        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * pow(rtol / E, 1.0 / 3.0));
+        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * cbrt_pos(rtol / E));
         sc.rejected = 1;
         sc.mlp_go = 0;
       }
