@@ -10,7 +10,13 @@
 //
 // Layout: states [T][N] (trajectory-major), j-vector operand [2T][N] with the
 // rows of trajectory b at 2b (sine) and 2b+1 (cosine), so that a 256-column
-// output tile holds both halves of 128 trajectories.
+// output tile holds both halves of 128 trajectories.  The operand is double
+// buffered: a stage reads one copy while its epilogue writes the next stage's
+// j-vector into the other (other CTAs of the launch may still be reading the
+// first).  The binary32 sine and cosine of every stage argument are kept
+// ([T][N] pairs) for the i-side finish of the next product, so the epilogue
+// does not reduce the phase again: binary64 arithmetic is scarce on GB300 and
+// the epilogue, not the tensor cores, bounds a stage.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -47,8 +53,9 @@ struct EArgs {
   double* K14;           // [2][T][N]: K1 and K4 slots
   double* K2;            // [T][N]
   double* K3;            // [T][N]
-  __nv_bfloat16* Vh;     // [2T][N]
+  __nv_bfloat16* Vh;     // [2T][N] j-vector operand the epilogue writes (the copy not being read)
   __nv_bfloat16* Vl;     // [2T][N]
+  float2* SC;            // [T][N] binary32 (sin, cos) of the current stage argument
   Traj tr;
   double rtol, atol, t1, hmax, hmin;
   long long max_attempts, max_rejects;
@@ -60,6 +67,7 @@ constexpr double kE1 = -5.0 / 72.0, kE2 = 1.0 / 12.0, kE3 = 1.0 / 9.0, kE4 = -1.
 __device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
   float s, c;
   sincos_f_of_d(y, &s, &c);
+  a.SC[(size_t)b * a.N + i] = make_float2(s, c);
   const __nv_bfloat16 sh = __float2bfloat16_rn(s), ch = __float2bfloat16_rn(c);
   const size_t rs = (size_t)(2 * b) * a.N + i, rc = rs + a.N;
   a.Vh[rs] = sh;
@@ -79,40 +87,38 @@ __device__ __forceinline__ double warp_max(double v) {
   return __longlong_as_double((long long)x);
 }
 
+// n / d for the error ratio, n >= 0: a binary32 reciprocal refined by one
+// Newton step in binary64 (relative error ~1e-14; three binary64 operations
+// instead of a correctly rounded division).  Outside [1e-30, 1e30] it divides.
+__device__ __forceinline__ double ratio(double n, double d) {
+  if (!(d >= 1e-30 && d <= 1e30)) return n / d;
+  const double r0 = (double)__frcp_rn((float)d);
+  return n * (r0 * fma(-d, r0, 2.0));
+}
+
 // The stage epilogue run on the accumulator rows of one 128 x 256 tile.
 struct Epilogue {
   EArgs a;
-  __device__ void operator()(int i, int col0, const float* v) const {
+  __device__ __forceinline__ void operator()(int i, int col0, const float* v) const {
     const int lane = threadIdx.x & 31;
     const int N = a.N, T = a.T;
-    (void)T;
-    for (int j = 0; j < 16; ++j) {
+    const size_t slot = (size_t)T * N;
+    const double thr = a.atol / a.rtol;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {   // unrolled: v[] stays in registers
       const int b = col0 / 2 + j;
       if (!a.tr.live[b]) continue;   // uniform over the warp
       const size_t o = (size_t)b * N + i;
-      const size_t slot = (size_t)T * N;
       const int xs = a.tr.xsel[b], ks = a.tr.ksel[b];
-      const double x = a.X[xs * slot + o];
-      const double k1 = a.K14[ks * slot + o];
-      double y;
-      switch (a.phase) {
-        case E_K1: y = x; break;
-        case E_F1: y = x + a.tr.h0[b] * k1; break;
-        case E_B2: y = x + a.tr.c21[b] * k1; break;
-        case E_B3: y = x + a.tr.c32[b] * a.K2[o]; break;
-        default: y = a.X[(1 - xs) * slot + o]; break;
-      }
-      float si, ci;
-      sincos_f_of_d(y, &si, &ci);
-      const float cpl = ci * v[2 * j] - si * v[2 * j + 1];
+      const float2 sc = a.SC[o];     // sin, cos of this stage's argument (agent i)
+      const float cpl = sc.y * v[2 * j] - sc.x * v[2 * j + 1];
       const double k = a.omega[o] + (double)cpl;
-      const double thr = a.atol / a.rtol;
-      double m = 0.0;
+      const double x = a.X[xs * slot + o];
       switch (a.phase) {
         case E_K1: {
           a.K14[ks * slot + o] = k;
-          const double sc = a.rtol * fmax(fabs(x), thr);
-          double m0 = warp_max(fabs(x) / sc), m1 = warp_max(fabs(k) / sc);
+          const double s = a.rtol * fmax(fabs(x), thr);
+          const double m0 = warp_max(fabs(x) / s), m1 = warp_max(fabs(k) / s);
           if (lane == 0) {
             atomicMax(&a.tr.red0[b], (unsigned long long)__double_as_longlong(m0));
             atomicMax(&a.tr.red1[b], (unsigned long long)__double_as_longlong(m1));
@@ -120,8 +126,8 @@ struct Epilogue {
           break;
         }
         case E_F1: {
-          const double sc = a.rtol * fmax(fabs(x), thr);
-          m = warp_max(fabs(k - k1) / sc);
+          const double s = a.rtol * fmax(fabs(x), thr);
+          const double m = warp_max(fabs(k - a.K14[ks * slot + o]) / s);
           if (lane == 0) atomicMax(&a.tr.red2[b], (unsigned long long)__double_as_longlong(m));
           break;
         }
@@ -131,6 +137,7 @@ struct Epilogue {
           break;
         case E_B3: {
           a.K3[o] = k;
+          const double k1 = a.K14[ks * slot + o];
           const double xn = x + a.tr.hs[b] * ((kB1 * k1 + kB2 * a.K2[o]) + kB3 * k);
           a.X[(1 - xs) * slot + o] = xn;
           put_v(a, b, i, xn);
@@ -138,11 +145,13 @@ struct Epilogue {
         }
         default: {
           a.K14[(1 - ks) * slot + o] = k;
+          const double k1 = a.K14[ks * slot + o];
+          const double y = a.X[(1 - xs) * slot + o];
           const double dv = a.tr.hs[b] * (((kE1 * k1 + kE2 * a.K2[o]) + kE3 * a.K3[o]) + kE4 * k);
           const double w = fmax(fmax(fabs(x), fabs(y)), thr);
-          double e = fabs(dv) / w;
+          double e = ratio(fabs(dv), w);
           if (!isfinite(y) || !isfinite(k)) e = __longlong_as_double(0x7ff8000000000000ll);
-          m = warp_max(e);
+          const double m = warp_max(e);
           if (lane == 0) atomicMax(&a.tr.emax[b], (unsigned long long)__double_as_longlong(m));
           break;
         }
@@ -151,12 +160,15 @@ struct Epilogue {
   }
 };
 
-__global__ void __launch_bounds__(tc::THREADS, 1)
+constexpr int kEpiWarps = 16;
+constexpr int kEnsThreads = tc::threads_for(kEpiWarps);
+
+__global__ void __launch_bounds__(kEnsThreads, 1)
     ens_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, EArgs a, int K,
                     int* err, long long spin) {
   const Epilogue epi{a};
-  tc::gemm_tile(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, epi, err, spin);
+  tc::gemm_tile<kEpiWarps>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, epi, err, spin);
 }
 
 // j-vector operand of the stage argument Y = X + c K1 (c = 0, h0 or h/2).
@@ -286,14 +298,14 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   cudaStream_t own = nullptr;   // graphs cannot be captured on the legacy default stream
   int rc = BS3_OK;
   const size_t NN = (size_t)N * N, TN = (size_t)T * N;
-  void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr;
+  void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr, *vh1 = nullptr, *vl1 = nullptr, *scb = nullptr;
   double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *K3 = nullptr, *dsc = nullptr;
   int *isc = nullptr, *derr = nullptr;
   long long* lsc = nullptr;
   unsigned long long* usc = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  CUtensorMap mAh, mAl, mBh, mBl;
+  CUtensorMap mAh, mAl, mBh, mBl, mBh1, mBl1;
   EArgs a;
   std::memset(&a, 0, sizeof(a));
   int herr = 0, any = 1;
@@ -311,6 +323,9 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   EN_CUDA(cudaMalloc(&kl, NN * 2));
   EN_CUDA(cudaMalloc(&vh, 2 * TN * 2));
   EN_CUDA(cudaMalloc(&vl, 2 * TN * 2));
+  EN_CUDA(cudaMalloc(&vh1, 2 * TN * 2));
+  EN_CUDA(cudaMalloc(&vl1, 2 * TN * 2));
+  EN_CUDA(cudaMalloc(&scb, TN * sizeof(float2)));
   EN_CUDA(cudaMalloc(&X, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K14, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K2, TN * sizeof(double)));
@@ -322,6 +337,9 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   EN_CUDA(cudaMalloc(&derr, sizeof(int)));
   EN_CUDA(cudaMemsetAsync(vh, 0, 2 * TN * 2, st));
   EN_CUDA(cudaMemsetAsync(vl, 0, 2 * TN * 2, st));
+  EN_CUDA(cudaMemsetAsync(vh1, 0, 2 * TN * 2, st));
+  EN_CUDA(cudaMemsetAsync(vl1, 0, 2 * TN * 2, st));
+  EN_CUDA(cudaMemsetAsync(scb, 0, TN * sizeof(float2), st));
   EN_CUDA(cudaMemsetAsync(isc, 0, (6 * T + 1) * sizeof(int), st));
   EN_CUDA(cudaMemsetAsync(lsc, 0, 3 * T * sizeof(long long), st));
   EN_CUDA(cudaMemsetAsync(usc, 0, 4 * T * sizeof(unsigned long long), st));
@@ -332,6 +350,8 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   EN_RC(tc_encode_bf16_2d(&mAl, kl, N, N, tc::BM));
   EN_RC(tc_encode_bf16_2d(&mBh, vh, 2 * T, N, tc::BN));
   EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, tc::BN));
+  EN_RC(tc_encode_bf16_2d(&mBh1, vh1, 2 * T, N, tc::BN));
+  EN_RC(tc_encode_bf16_2d(&mBl1, vl1, 2 * T, N, tc::BN));
   EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
   a.N = (int)N;
   a.T = (int)T;
@@ -342,6 +362,7 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   a.K3 = K3;
   a.Vh = (__nv_bfloat16*)vh;
   a.Vl = (__nv_bfloat16*)vl;
+  a.SC = (float2*)scb;
   a.tr.t = dsc; a.tr.h = dsc + T; a.tr.h0 = dsc + 2 * T; a.tr.c21 = dsc + 3 * T; a.tr.c32 = dsc + 4 * T;
   a.tr.hs = dsc + 5 * T;
   a.tr.live = isc; a.tr.xsel = isc + T; a.tr.ksel = isc + 2 * T; a.tr.last = isc + 3 * T; a.tr.rej = isc + 4 * T;
@@ -364,25 +385,36 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
     EN_CUDA(cudaStreamSynchronize(st));
   }
   // ---- K1 = f(t0, y0) and the starting step of every trajectory
+  // (j-vector operand copy 0 throughout; these epilogues write no j-vector)
+  a.Vh = (__nv_bfloat16*)vh;
+  a.Vl = (__nv_bfloat16*)vl;
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
   a.phase = E_K1;
-  ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
   a.phase = E_F1;
-  ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
   EN_CUDA(cudaGetLastError());
-  // ---- U attempts per graph: prologue (Y2), three fused stages, control
+  // ---- U attempts per graph: prologue (Y2 -> copy 0), stage 2 (reads copy 0,
+  // writes Y3 to copy 1), stage 3 (reads copy 1, writes X' to copy 0), stage 4
+  // (reads copy 0), control
   EN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   for (int u = 0; u < U; ++u) {
+    a.Vh = (__nv_bfloat16*)vh;
+    a.Vl = (__nv_bfloat16*)vl;
     ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 2);
     a.phase = E_B2;
-    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    a.Vh = (__nv_bfloat16*)vh1;
+    a.Vl = (__nv_bfloat16*)vl1;
+    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     a.phase = E_B3;
-    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    a.Vh = (__nv_bfloat16*)vh;
+    a.Vl = (__nv_bfloat16*)vl;
+    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
     a.phase = E_B4;
-    ens_gemm_kernel<<<ggrid, tc::THREADS, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
     ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
   }
@@ -411,7 +443,7 @@ done:
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
-  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
+  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
   cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
   return rc;
 }

@@ -5,7 +5,9 @@
 // binary32 in tensor memory.  One CTA computes a 128 x 256 tile:
 //   warp 0: TMA producer (2D tiles, 128-byte swizzle, two-stage ring);
 //   warp 1: allocates tensor memory and issues tcgen05.mma (one thread);
-//   warps 2-5: epilogue, tcgen05.ld of the accumulator rows.
+//   warps 2 .. 2+EW-1: epilogue, tcgen05.ld of the accumulator rows (warp w
+//   reads tensor-memory lanes 32*(w%4) .. +31; EW/4 warps share each lane
+//   quarter and split its 32-column chunks).
 // Every wait is bounded; a wait that runs out sets *err and the CTA winds down.
 #pragma once
 
@@ -21,7 +23,8 @@ constexpr int A_BYTES = BM * BK * 2;                  // 16 KB per bf16 operand 
 constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int THREADS = 192;
+constexpr int THREADS = 192;                      // plain product: four epilogue warps
+constexpr int threads_for(int ew) { return 64 + 32 * ew; }
 constexpr int TMEM_COLS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -110,7 +113,7 @@ struct StoreRowMajor {
   }
 };
 
-template <class Store>
+template <int EW, class Store>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensorMap* mAl, const CUtensorMap* mBh,
                                           const CUtensorMap* mBl, int m0, int n0, int K, const Store& store,
                                           int* err, long long spin) {
@@ -193,14 +196,16 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
     mma_commit(done);   // fires when every MMA issued above has completed
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
+    static_assert(EW % 4 == 0 && EW >= 4 && EW <= 32, "epilogue warps: a multiple of four");
     const bool ok = mbar_wait(done, 0, spin);
     fence_after();
     if (!ok) atomicExch(err, 1);
     if (ok && !*(volatile int*)s_abort) {
       const int quarter = warp & 3;   // tensor-memory lanes 32*quarter .. 32*quarter+31
+      const int sub = (warp - 2) >> 2;   // which of the EW/4 warps of this quarter
       const int row = m0 + quarter * 32 + lane;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = sub; c < BN / 32; c += EW / 4) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), v);
         store(row, n0 + c * 32, v);
