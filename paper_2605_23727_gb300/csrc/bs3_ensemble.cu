@@ -96,64 +96,76 @@ __device__ __forceinline__ double ratio(double n, double d) {
   return n * (r0 * fma(-d, r0, 2.0));
 }
 
-// The stage epilogue run on the accumulator rows of one 128 x 256 tile.
+// The stage epilogue run on the accumulator rows of one 128 x 256 tile, one
+// instantiation per phase.  Each thread owns one row i and 16 trajectories
+// per call; the inputs of four trajectories are loaded together (also for
+// retired trajectories, whose buffers stay allocated) so that the loads
+// overlap, and only live trajectories are written.
+template <int PH>
 struct Epilogue {
   EArgs a;
   __device__ __forceinline__ void operator()(int i, int col0, const float* v) const {
+    constexpr int G = 4;
     const int lane = threadIdx.x & 31;
-    const int N = a.N, T = a.T;
-    const size_t slot = (size_t)T * N;
+    const int N = a.N;
+    const size_t slot = (size_t)a.T * N;
     const double thr = a.atol / a.rtol;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {   // unrolled: v[] stays in registers
-      const int b = col0 / 2 + j;
-      if (!a.tr.live[b]) continue;   // uniform over the warp
-      const size_t o = (size_t)b * N + i;
-      const int xs = a.tr.xsel[b], ks = a.tr.ksel[b];
-      const float2 sc = a.SC[o];     // sin, cos of this stage's argument (agent i)
-      const float cpl = sc.y * v[2 * j] - sc.x * v[2 * j + 1];
-      const double k = a.omega[o] + (double)cpl;
-      const double x = a.X[xs * slot + o];
-      switch (a.phase) {
-        case E_K1: {
-          a.K14[ks * slot + o] = k;
-          const double s = a.rtol * fmax(fabs(x), thr);
-          const double m0 = warp_max(fabs(x) / s), m1 = warp_max(fabs(k) / s);
+    for (int j0 = 0; j0 < 16; j0 += G) {
+      int live[G], xs[G], ks[G];
+      double x[G], om[G], k1[G], k2[G], k3[G], y[G];
+      float2 sc[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int b = col0 / 2 + j0 + g;
+        const size_t o = (size_t)b * N + i;
+        live[g] = a.tr.live[b];
+        xs[g] = a.tr.xsel[b];
+        ks[g] = a.tr.ksel[b];
+        sc[g] = a.SC[o];   // sin, cos of this stage's argument (agent i)
+        om[g] = a.omega[o];
+        x[g] = a.X[xs[g] * slot + o];
+        k1[g] = (PH == E_F1 || PH == E_B3 || PH == E_B4) ? a.K14[ks[g] * slot + o] : 0.0;
+        k2[g] = (PH == E_B3 || PH == E_B4) ? a.K2[o] : 0.0;
+        k3[g] = (PH == E_B4) ? a.K3[o] : 0.0;
+        y[g] = (PH == E_B4) ? a.X[(1 - xs[g]) * slot + o] : 0.0;
+      }
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int j = j0 + g;
+        const int b = col0 / 2 + j;
+        if (!live[g]) continue;   // uniform over the warp
+        const size_t o = (size_t)b * N + i;
+        const float cpl = sc[g].y * v[2 * j] - sc[g].x * v[2 * j + 1];
+        const double k = om[g] + (double)cpl;
+        if (PH == E_K1) {
+          a.K14[ks[g] * slot + o] = k;
+          const double s = a.rtol * fmax(fabs(x[g]), thr);
+          const double m0 = warp_max(fabs(x[g]) / s), m1 = warp_max(fabs(k) / s);
           if (lane == 0) {
             atomicMax(&a.tr.red0[b], (unsigned long long)__double_as_longlong(m0));
             atomicMax(&a.tr.red1[b], (unsigned long long)__double_as_longlong(m1));
           }
-          break;
-        }
-        case E_F1: {
-          const double s = a.rtol * fmax(fabs(x), thr);
-          const double m = warp_max(fabs(k - a.K14[ks * slot + o]) / s);
+        } else if (PH == E_F1) {
+          const double s = a.rtol * fmax(fabs(x[g]), thr);
+          const double m = warp_max(fabs(k - k1[g]) / s);
           if (lane == 0) atomicMax(&a.tr.red2[b], (unsigned long long)__double_as_longlong(m));
-          break;
-        }
-        case E_B2:
+        } else if (PH == E_B2) {
           a.K2[o] = k;
-          put_v(a, b, i, x + a.tr.c32[b] * k);
-          break;
-        case E_B3: {
+          put_v(a, b, i, x[g] + a.tr.c32[b] * k);
+        } else if (PH == E_B3) {
           a.K3[o] = k;
-          const double k1 = a.K14[ks * slot + o];
-          const double xn = x + a.tr.hs[b] * ((kB1 * k1 + kB2 * a.K2[o]) + kB3 * k);
-          a.X[(1 - xs) * slot + o] = xn;
+          const double xn = x[g] + a.tr.hs[b] * ((kB1 * k1[g] + kB2 * k2[g]) + kB3 * k);
+          a.X[(1 - xs[g]) * slot + o] = xn;
           put_v(a, b, i, xn);
-          break;
-        }
-        default: {
-          a.K14[(1 - ks) * slot + o] = k;
-          const double k1 = a.K14[ks * slot + o];
-          const double y = a.X[(1 - xs) * slot + o];
-          const double dv = a.tr.hs[b] * (((kE1 * k1 + kE2 * a.K2[o]) + kE3 * a.K3[o]) + kE4 * k);
-          const double w = fmax(fmax(fabs(x), fabs(y)), thr);
+        } else {
+          a.K14[(1 - ks[g]) * slot + o] = k;
+          const double dv = a.tr.hs[b] * (((kE1 * k1[g] + kE2 * k2[g]) + kE3 * k3[g]) + kE4 * k);
+          const double w = fmax(fmax(fabs(x[g]), fabs(y[g])), thr);
           double e = ratio(fabs(dv), w);
-          if (!isfinite(y) || !isfinite(k)) e = __longlong_as_double(0x7ff8000000000000ll);
+          if (!isfinite(y[g]) || !isfinite(k)) e = __longlong_as_double(0x7ff8000000000000ll);
           const double m = warp_max(e);
           if (lane == 0) atomicMax(&a.tr.emax[b], (unsigned long long)__double_as_longlong(m));
-          break;
         }
       }
     }
@@ -163,11 +175,12 @@ struct Epilogue {
 constexpr int kEpiWarps = 16;
 constexpr int kEnsThreads = tc::threads_for(kEpiWarps);
 
+template <int PH>
 __global__ void __launch_bounds__(kEnsThreads, 1)
     ens_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, EArgs a, int K,
                     int* err, long long spin) {
-  const Epilogue epi{a};
+  const Epilogue<PH> epi{a};
   tc::gemm_tile<kEpiWarps>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, epi, err, spin);
 }
 
@@ -352,7 +365,11 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, tc::BN));
   EN_RC(tc_encode_bf16_2d(&mBh1, vh1, 2 * T, N, tc::BN));
   EN_RC(tc_encode_bf16_2d(&mBl1, vl1, 2 * T, N, tc::BN));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
   a.N = (int)N;
   a.T = (int)T;
   a.omega = omega;
@@ -390,11 +407,11 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   a.Vl = (__nv_bfloat16*)vl;
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
   a.phase = E_K1;
-  ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_K1><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
   a.phase = E_F1;
-  ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_F1><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
   EN_CUDA(cudaGetLastError());
   // ---- U attempts per graph: prologue (Y2 -> copy 0), stage 2 (reads copy 0,
@@ -408,13 +425,13 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
     a.phase = E_B2;
     a.Vh = (__nv_bfloat16*)vh1;
     a.Vl = (__nv_bfloat16*)vl1;
-    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B2><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     a.phase = E_B3;
     a.Vh = (__nv_bfloat16*)vh;
     a.Vl = (__nv_bfloat16*)vl;
-    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B3><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
     a.phase = E_B4;
-    ens_gemm_kernel<<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B4><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
     ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
   }
