@@ -64,7 +64,17 @@ CASES = {
     "ragged1000_lco_mixed1_f16": None,
     "proposer_lco32768_f16": None,
     "proposer_lco8192_f16": None,
+    "phases_kuramoto4096_mixed1_f32": None,
+    "sweep_kuramoto4096": None,
 }
+
+# FP32 instructions per pair of the circadian coupling (own arctangent): the
+# difference, reciprocal (above 1) with its selects, z = t*t, 8 polynomial FMAs,
+# the product t*P, the pi/2 fold and sign, and the FMA with the weight.
+CC_OPS_PER_PAIR = 15
+# binary32 lanes per SM and the maximum SM clock of GB300 (nominal ALU peak)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
 
 
 def run_ensemble_case(name):
@@ -173,9 +183,116 @@ def run_proposer_case(name):
     print(json.dumps(out))
 
 
+def run_phases_case(name):
+    """Per-phase device time of the attempts of the benchmark solve (Kuramoto
+    N=4096, Mixed1, f32 weights), from the library's step records: the time
+    from the start of an attempt to the end of each of its four grid barriers
+    (A: Y2 j-vector; B2, B3: stages 2, 3; B4: stage 4 and the error norm), and
+    the rest (decision and the next attempt's set-up)."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    out = {"case": name}
+    for N, t1 in ((4096, T1), (256, 5.0)):
+        w = workloads.kuramoto(N, 0, t1=t1, rtol=RTOL)
+        s = bs3.System.from_workload(w, "f32")
+        y0 = torch.tensor(w.y0, device="cuda")
+        yo = torch.empty_like(y0)
+        cap = 1 << 15
+        bs3.bs3_set_history(s.handle, cap)
+        for _ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, RTOL, RTOL, bs3.MIXED1, bs3.ACC_FLOAT2, None, 0,
+                                   None, yo, 0)
+            e1.record()
+            e1.synchronize()
+        rc2, H = bs3.bs3_get_history(s.handle, cap)
+        s.close()
+        att = st.n_accepted + st.n_rejected
+        per = 1e3 * e0.elapsed_time(e1) / att
+        cum = np.median(H[2:, 4:8], axis=0) / 1e3
+        ph = np.diff(np.concatenate([[0.0], cum]))
+        out[f"N{N}"] = {"status": bs3.bs3_status_string(rc), "attempts": att, "us_per_attempt": per,
+                        "us_A_Y2": ph[0], "us_B2": ph[1], "us_B3": ph[2], "us_B4_error": ph[3],
+                        "us_decision_and_setup": per - cum[3]}
+    print(json.dumps(out))
+
+
+def run_sweep_case(name):
+    """Time-to-solution against global error: every variant x stored format
+    over rtol = atol = 1e-3 .. 1e-9 on the benchmark workload (Kuramoto
+    N=4096, t in [0, 50]), global error against the oracle's DOPRI5 reference;
+    then each mixed variant's time at the global error the binary64 path
+    reaches, by log-log interpolation along the variant's own curve."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    w = workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL)
+    ref = np.load(REF_FILE)
+    y0 = torch.tensor(w.y0, device="cuda")
+    yo = torch.empty_like(y0)
+    rtols = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9]
+    combos = [("double", "f64"), ("mixed2", "f32"), ("mixed1", "f32"), ("single", "f32"),
+              ("mixed2", "bf16"), ("mixed1", "bf16"), ("mixed1", "f16")]
+    curves = {}
+    for variant, store in combos:
+        s = bs3.System.from_workload(w, store)
+        pts = []
+        for rt in rtols:
+            times = []
+            for _ in range(2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0, rt, rt, bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2,
+                                       None, 0, None, yo, 0)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            err = normalized_error(yo.cpu().numpy(), ref, w.N) if rc == bs3.OK else None
+            rec = {"variant": variant, "weights": store, "rtol": rt, "status": bs3.bs3_status_string(rc),
+                   "ms": min(times), "global_error": err, "accepted": st.n_accepted, "rejected": st.n_rejected,
+                   "rhs_evals": st.n_rhs_evals}
+            print(json.dumps(rec), flush=True)
+            if rc == bs3.OK:
+                pts.append((err, min(times)))
+        s.close()
+        curves[f"{variant}/{store}"] = pts
+
+    def time_at(pts, e):
+        # log-log interpolation between the two points bracketing error e
+        for (e_a, t_a), (e_b, t_b) in zip(pts, pts[1:]):
+            lo, hi = min(e_a, e_b), max(e_a, e_b)
+            if lo <= e <= hi and e_a != e_b:
+                f = (math.log(e) - math.log(e_a)) / (math.log(e_b) - math.log(e_a))
+                return math.exp(math.log(t_a) + f * (math.log(t_b) - math.log(t_a)))
+        return None
+
+    summary = []
+    for e_target, t_double in curves["double/f64"]:
+        row = {"global_error": e_target, "double_ms": t_double}
+        for key, pts in curves.items():
+            if key == "double/f64":
+                continue
+            t = time_at(pts, e_target)
+            row[key] = None if t is None else {"ms": t, "speedup_vs_double": t_double / t}
+        summary.append(row)
+    print(json.dumps({"case": name, "time_at_double_error": summary}))
+
+
 def run_case(name):
     if name.startswith("ensemble"):
         return run_ensemble_case(name)
+    if name.startswith("phases"):
+        return run_phases_case(name)
+    if name.startswith("sweep"):
+        return run_sweep_case(name)
     if name.startswith("ragged"):
         return run_ragged_case(name)
     if name.startswith("proposer"):
@@ -199,10 +316,20 @@ def run_case(name):
     e1.record()
     e1.synchronize()
     sysm.close()
-    print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "ms": e0.elapsed_time(e1),
-                      "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals,
-                      "N": w.N, "weights": store, "variant": variant,
-                      "weight_bytes_per_eval": w.N * w.N * STORE_BYTES[store]}))
+    ms = e0.elapsed_time(e1)
+    out = {"case": name, "status": bs3.bs3_status_string(rc), "ms": ms,
+           "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals,
+           "us_per_attempt": 1e3 * ms / max(1, st.n_accepted + st.n_rejected),
+           "N": w.N, "weights": store, "variant": variant,
+           "weight_bytes_per_eval": w.N * w.N * STORE_BYTES[store]}
+    if w.kind == "circadian":
+        # FP32 ALU roofline of the pairwise arctangent coupling
+        ops = float(st.n_rhs_evals) * w.N * w.N * CC_OPS_PER_PAIR
+        peak = 152 * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+        out["alu"] = {"ops_per_pair": CC_OPS_PER_PAIR, "achieved_Tops": ops / (ms * 1e-3) / 1e12,
+                      "peak_Tops": peak / 1e12, "frac": ops / (ms * 1e-3) / peak,
+                      "peak_basis": "nominal: 152 SMs x 128 binary32 lanes x 2070 MHz"}
+    print(json.dumps(out))
     if rc != bs3.OK:
         sys.exit(1)
 
@@ -228,14 +355,21 @@ def dist_env():
     return rank, world, local
 
 
-def csrc_sha256():
+# Sources that decide the code and launch plan of each profiled kernel; a
+# capture's DRAM traffic is reported only while these are unchanged.
+KERNEL_SOURCES = {
+    "solver": ("bs3_device.cuh", "bs3_solver.cuh", "bs3_mlp.cuh", "bs3_api.cu", "gen_inst.py"),
+    "ensemble": ("bs3_device.cuh", "bs3_tc.cuh", "bs3_tc_host.h", "bs3_tc.cu", "bs3_ensemble.cu"),
+}
+
+
+def kernel_sha256(which="solver"):
     import hashlib
     csrc = os.path.join(ROOT, "paper_2605_23727_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[which]:
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()
 
 
@@ -246,7 +380,7 @@ def recorded_traffic(case):
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(case)
-    if not rec or rec.get("csrc_sha256") != csrc_sha256():
+    if not rec or rec.get("sources_sha256") != kernel_sha256(rec.get("sources", "solver")):
         return None
     return rec["dram_bytes_per_launch"]
 
