@@ -237,12 +237,27 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
     xi32[r] = DD ? 0.f : v32[i];
     xi64[r] = DD ? v64[i] : 0.0;
   }
+  // the weight chunks of the next iteration are loaded before the current
+  // one's arctangents run, so the stream's latency hides behind them
+  uint4 nxt[RB];
+  {
+    const int col = lt * VEC;
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      nxt[r] = (r < nrows && col < a.ld)
+                   ? ld_stream16_pol(qb + (size_t)(row0 + r) * rstride + (size_t)col * L::BYTES, pol)
+                   : make_uint4(0u, 0u, 0u, 0u);
+  }
   for (int col = lt * VEC; col < a.ld; col += gt * VEC) {
     uint4 raw[RB];
 #pragma unroll
+    for (int r = 0; r < RB; ++r) raw[r] = nxt[r];
+    const int ncol = col + gt * VEC;
+#pragma unroll
     for (int r = 0; r < RB; ++r)
-      raw[r] = (r < nrows) ? ld_stream16_pol(qb + (size_t)(row0 + r) * rstride + (size_t)col * L::BYTES, pol)
-                           : make_uint4(0u, 0u, 0u, 0u);
+      nxt[r] = (r < nrows && ncol < a.ld)
+                   ? ld_stream16_pol(qb + (size_t)(row0 + r) * rstride + (size_t)ncol * L::BYTES, pol)
+                   : make_uint4(0u, 0u, 0u, 0u);
     if (!DD) {
       float xj[VEC];
 #pragma unroll

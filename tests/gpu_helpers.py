@@ -47,7 +47,7 @@ def rhs_tolerance(osys, y, prec, accum="float2"):
     """Per-component bound on |gpu - oracle| for one right-hand side.
 
     * the j-side values and products agree to a few units of the G
-      precision (own arctangent <= 2 ulp, sincos of a reduced phase <= 2 ulp);
+      precision (own arctangent <= 3 ulp, sincos of a reduced phase <= 2 ulp);
     * binary32 sums (Sigma = S) may be ordered differently: at most
       (N + 64) binary32 roundings of sum_j |w_ij g_j|;
     * binary64 / float-float sums: (N + 64) roundings of their own unit;
