@@ -62,6 +62,7 @@ CASES = {
     "ensemble256_kuramoto8192": None,
     "ensemble128_kuramoto1024": None,
     "ragged1000_lco_mixed1_f16": None,
+    "ragged_skewed_lco_f16": None,
     "proposer_lco32768_f16": None,
     "proposer_lco8192_f16": None,
     "phases_kuramoto4096_mixed1_f32": None,
@@ -134,6 +135,46 @@ def run_ragged_case(name):
                       "weight_GBs": weight_bytes / (kms * 1e-3) / 1e9, "all_ok": all(st.status == 0 for st in stats)}))
     if rc != bs3.OK:
         sys.exit(1)
+
+
+def run_skewed_case(name):
+    """A skewed ragged batch: one second-order oscillator system of N=8192
+    among 200 of N=256 (f16, Mixed1, t in [0, 2]).  The large system is
+    solved by a team of CTAs; its solve alone through bs3_solve (the whole
+    GPU) is timed beside the batch."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    systems = [workloads.lco_config(8192, 1, t1=2.0, rtol=RTOL)] + \
+        [workloads.lco_config(256, 2 + k, t1=2.0, rtol=RTOL) for k in range(200)]
+    Ns = [w.N for w in systems]
+    K = np.concatenate([np.asarray(w.coupling, dtype=np.float32).ravel() for w in systems])
+    params = np.concatenate([w.params for w in systems])
+    y0 = np.concatenate([w.y0 for w in systems])
+    S = len(systems)
+    args = (bs3.LCO_CFG, Ns, params, K, bs3.F16, y0, np.zeros(S), np.full(S, 2.0), RTOL, RTOL, bs3.MIXED1,
+            bs3.ACC_FLOAT2)
+    bs3.bs3_batch_solve(*args)
+    rc, yf, stats, kms = bs3.bs3_batch_solve(*args)
+    big = systems[0]
+    s = bs3.System.from_workload(big, "f16")
+    y0d = torch.tensor(big.y0, device="cuda")
+    yo = torch.empty_like(y0d)
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc2, st = bs3.bs3_solve(s.handle, big.t0, big.t1, y0d, RTOL, RTOL, bs3.MIXED1, bs3.ACC_FLOAT2, None, 0,
+                                None, yo, 0)
+        e1.record()
+        e1.synchronize()
+    s.close()
+    print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "batch_kernel_ms": kms,
+                      "big_alone_ms": e0.elapsed_time(e1), "big_attempts_in_batch": stats[0].n_accepted +
+                      stats[0].n_rejected, "big_attempts_alone": st.n_accepted + st.n_rejected,
+                      "big_max_abs_diff": float(np.max(np.abs(yf[:2 * 8192] - yo.cpu().numpy())))}))
 
 
 def run_proposer_case(name):
@@ -293,6 +334,8 @@ def run_case(name):
         return run_phases_case(name)
     if name.startswith("sweep"):
         return run_sweep_case(name)
+    if name.startswith("ragged_skewed"):
+        return run_skewed_case(name)
     if name.startswith("ragged"):
         return run_ragged_case(name)
     if name.startswith("proposer"):

@@ -250,6 +250,48 @@ int pick_grid(bs3_system* s) {
   return BS3_OK;
 }
 
+// Launch plan of a ragged batch (systems sorted by decreasing N).  The cost
+// of a system is N^2 (weight bytes per evaluation); a system above the mean
+// cost per CTA would keep one SM busy long after the others finish, so such
+// systems go to teams of `team` CTAs, team = ceil(largest cost / mean cost)
+// (at most 8, and at least 64 rows per CTA); the teams get the CTAs in
+// proportion to the big systems' share of the cost.
+constexpr int kMaxTeams = 256;
+
+struct BatchPlan {
+  int grid, n_big, team, n_teams;
+};
+
+BatchPlan plan_batch(const std::vector<int64_t>& sortedN, int sms) {
+  const int64_t S = (int64_t)sortedN.size();
+  BatchPlan p{(int)std::min<int64_t>(sms, S), 0, 1, 0};
+  double total = 0.0;
+  for (int64_t n : sortedN) total += (double)n * (double)n;
+  if (sms < 4 || S < 1) return p;
+  const double share = total / sms;
+  const double big0 = (double)sortedN[0] * (double)sortedN[0];
+  int team = (int)std::ceil(big0 / share);
+  team = std::min<int>(team, 8);
+  team = std::min<int64_t>(team, std::max<int64_t>(1, sortedN[0] / 64));
+  if (team < 2) return p;
+  int n_big = 0;
+  double big = 0.0;
+  while (n_big < S && (double)sortedN[n_big] * (double)sortedN[n_big] > share) {
+    big += (double)sortedN[n_big] * (double)sortedN[n_big];
+    ++n_big;
+  }
+  int ctas = (int)std::lround(sms * big / total);
+  ctas = std::max(ctas, team);
+  ctas = std::min(ctas, n_big < S ? sms - 1 : sms);
+  int n_teams = std::min<int>(std::min(ctas / team, n_big), kMaxTeams);
+  if (n_teams < 1) return p;
+  p.grid = sms;
+  p.n_big = n_big;
+  p.team = team;
+  p.n_teams = n_teams;
+  return p;
+}
+
 void fill_args(const bs3_system* s, Args& a) {
   std::memset(&a, 0, sizeof(a));
   a.N = (int)s->N;
@@ -441,7 +483,9 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
                oTh = take(TN * 8), oY0 = take((size_t)d * TN * 8), oYF = take((size_t)d * TN * 8),
                oState = take((size_t)6 * d * TN * 8), oJ32 = take((size_t)6 * offL[S] * 4),
                oJ64 = take((size_t)6 * offL[S] * 8), oCtl = take((size_t)S * sizeof(Control)),
-               oDesc = take((size_t)S * sizeof(SysDesc)), oNext = take(sizeof(int));
+               oDesc = take((size_t)S * sizeof(SysDesc)), oNext = take(sizeof(int)), oBigNext = take(sizeof(int)),
+               oTeamJob = take(kMaxTeams * sizeof(int)), oTeamBar = take(kMaxTeams * sizeof(unsigned long long)),
+               oTeamStatus = take(kMaxTeams * sizeof(int));
   std::vector<SysDesc> desc(S);
   std::vector<int64_t> order(S);
   std::vector<double> par_h(TN), th_h(TN);
@@ -460,7 +504,9 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
     if (cudaMemsetAsync(arena + oJ32, 0, (size_t)6 * offL[S] * 4, st) != cudaSuccess ||
         cudaMemsetAsync(arena + oJ64, 0, (size_t)6 * offL[S] * 8, st) != cudaSuccess ||
         cudaMemsetAsync(arena + oCtl, 0, (size_t)S * sizeof(Control), st) != cudaSuccess ||
-        cudaMemsetAsync(arena + oNext, 0, sizeof(int), st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+        cudaMemsetAsync(arena + oNext, 0, oTeamStatus + kMaxTeams * sizeof(int) - oNext, st) != cudaSuccess) {
+      rc = BS3_ERR_CUDA; break;
+    }
     // per-agent parameters (and k1/(k0-k1) for the circadian kind)
     double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = 0; k < S; ++k) {
@@ -530,21 +576,35 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
     a.hmin = 100.0 * (variant == BS3_SINGLE ? (double)FLT_EPSILON : DBL_EPSILON);
     a.max_attempts = 100000;
     a.max_rejects = 85000;
-    a.spin_limit = 1;
     a.l2_keep = 0;
     if (kind == BS3_CIRCADIAN)
       for (int q = 0; q < 8; ++q) a.g[q] = params[offP[0] + Ns[0] + q];   // constants shared by the batch
     ba.sys = (const SysDesc*)(arena + oDesc);
     ba.S = (int)S;
     ba.next = (int*)(arena + oNext);
+    ba.big_next = (int*)(arena + oBigNext);
+    ba.team_job = (int*)(arena + oTeamJob);
+    ba.team_bar = (unsigned long long*)(arena + oTeamBar);
+    ba.team_status = (int*)(arena + oTeamStatus);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
-    const unsigned grid = (unsigned)std::min<int64_t>(sms, S);
+    // teams of CTAs for the systems too large for one SM's share of the batch
+    // (cost ~ N^2: the weight bytes each evaluation streams)
+    std::vector<int64_t> sortedN(S);
+    for (int64_t k = 0; k < S; ++k) sortedN[k] = Ns[order[k]];
+    const BatchPlan plan = plan_batch(sortedN, sms);
+    ba.n_big = plan.n_big;
+    ba.team = plan.team;
+    ba.n_teams = plan.n_teams;
+    a.spin_limit = (long long)1 << 26;
+    const unsigned grid = (unsigned)plan.grid;
     void* kargs[] = {&ba};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (kernel_ms && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess ||
                       cudaEventRecord(ev0, st) != cudaSuccess)) { rc = BS3_ERR_CUDA; break; }
-    if (cudaLaunchKernel(batch_kernel_lookup(kind, store), dim3(grid), dim3(kBlock), kargs, 0, st) != cudaSuccess) {
+    // cooperative: the CTAs of a team wait on one another
+    if (cudaLaunchCooperativeKernel(batch_kernel_lookup(kind, store), dim3(grid), dim3(kBlock), kargs, 0, st) !=
+        cudaSuccess) {
       rc = BS3_ERR_CUDA; break;
     }
     if (kernel_ms) {
@@ -555,6 +615,9 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
       cudaEventDestroy(ev0);
       cudaEventDestroy(ev1);
     }
+    std::vector<int> team_status(kMaxTeams, 0);
+    if (cudaMemcpyAsync(team_status.data(), arena + oTeamStatus, kMaxTeams * sizeof(int), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
     if (cudaMemcpyAsync(y_final, arena + oYF, (size_t)d * TN * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(ctl.data(), arena + oCtl, S * sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
@@ -571,6 +634,8 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
       }
       if (ctl[k].status != BS3_OK && worst == BS3_OK) worst = ctl[k].status;
     }
+    for (int t = 0; t < kMaxTeams; ++t)
+      if (team_status[t] != 0 && worst == BS3_OK) worst = BS3_ERR_DEVICE_WAIT;
     rc = worst;
   } while (0);
   cudaFree(arena);

@@ -116,21 +116,23 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   return v;
 }
 
-__device__ __forceinline__ bool grid_sync(Control* c, unsigned long long& target,
-                                          long long spin_limit, int* s_abort) {
+// Barrier of nb co-resident CTAs on one monotonic counter (the whole grid,
+// or a team of CTAs that solves one system of a batch).
+__device__ __forceinline__ bool group_sync(unsigned long long* counter, int* status, unsigned long long& target,
+                                           int nb, long long spin_limit, int* s_abort) {
   __syncthreads();
-  target += gridDim.x;
+  target += nb;
   if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" :: "l"(&c->bar) : "memory");
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" :: "l"(counter) : "memory");
     long long it = 0;
     int abort = 0;
     while (true) {
-      const unsigned long long v = ld_acquire_u64(&c->bar);
+      const unsigned long long v = ld_acquire_u64(counter);
       if (v >= kAbortBias) { abort = 1; break; }
       if (v >= target) break;
       if (++it > spin_limit) {
-        atomicCAS(&c->status, 0, (int)S_DEVICE_WAIT);
-        atomicAdd(&c->bar, kAbortBias);
+        atomicCAS(status, 0, (int)S_DEVICE_WAIT);
+        atomicAdd(counter, kAbortBias);
         abort = 1;
         break;
       }
@@ -140,6 +142,11 @@ __device__ __forceinline__ bool grid_sync(Control* c, unsigned long long& target
   }
   __syncthreads();
   return !*s_abort;
+}
+
+__device__ __forceinline__ bool grid_sync(Control* c, unsigned long long& target, int nb,
+                                          long long spin_limit, int* s_abort) {
+  return group_sync(&c->bar, &c->status, target, nb, spin_limit, s_abort);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {

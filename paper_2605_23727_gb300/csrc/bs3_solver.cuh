@@ -409,6 +409,7 @@ struct Ctx {
   double* srs;        // shared row sums
   float* sscale;      // shared row scales
   int rc, rb, nr;
+  int rank, nb;      // this CTA's place in the group of CTAs that solves the system (nb = 1: alone)
   int iX, iXn, iK1, iK2, iK3, iK4;
   double c21, c32, hs, h0s, thr, rtol;
   Prec p;    // precision of the stage being evaluated
@@ -639,28 +640,28 @@ __device__ __forceinline__ int group_threads(int rc) {
   return gt;
 }
 
-// Grid-wide barrier (persistent launch over all SMs) or CTA barrier (a CTA
-// that solves one system alone).
-template <bool CTA>
-__device__ __forceinline__ bool sync_all(Control* c, unsigned long long& target, long long spin_limit, int* s_abort) {
-  if (CTA) {
+// Barrier of the CTAs that solve the system: a CTA barrier when one CTA
+// solves it alone, otherwise the group barrier on the system's counter.
+__device__ __forceinline__ bool sync_all(const Ctx& x, Control* c, unsigned long long& target, long long spin_limit,
+                                         int* s_abort) {
+  if (x.nb == 1) {
     __syncthreads();
     return true;
   }
-  return grid_sync(c, target, spin_limit, s_abort);
+  return grid_sync(c, target, x.nb, spin_limit, s_abort);
 }
 
 // A job (RHS, one attempt or a whole solve) on the agents [x.rb, x.rb + x.nr)
-// whose state x already holds.  CTA = false: the agents of one system are
-// spread over the whole grid; CTA = true: this CTA owns all of them.
-template <int KIND, int ST, bool CTA>
+// whose state x already holds; the system's agents are spread over x.nb CTAs
+// (the whole grid, a team of a batch, or this CTA alone).
+template <int KIND, int ST>
 __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_abort, unsigned long long* s_red,
                                         unsigned long long* s_grp, const float* smlp) {
   constexpr int d = Dim<KIND>::d;
   const int N = a.N;
-  const int b = blockIdx.x;
+  const int b = x.rank;
   const int tid = threadIdx.x;
-  const bool leader = CTA ? (tid == 0) : (b == 0 && tid == 0);
+  const bool leader = (b == 0 && tid == 0);
   Control* ctrl = a.ctrl;
   unsigned long long bt = 0;
   const bool single = x.single;
@@ -673,7 +674,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
       put_jv<KIND>(a, 0, x.rb + li, Y, x.p.g, single);
     }
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) return;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) return;
     stage<KIND, ST>(a, x, PH_RHS, 0, s_grp);
     return;
   }
@@ -700,7 +701,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       put_jv<KIND>(a, 0, x.rb + li, Y, p4.g, single);
     }
   }
-  if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
+  if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
 
   if (a.job == JOB_SOLVE) {
     // ---- K1 = f(t0, y0) with the k4 row; starting-step norms d0, d1
@@ -709,7 +710,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
     stage<KIND, ST>(a, x, PH_K1, 0, s_grp);
     block_max(x.m0, &ctrl->red[0], s_red);
     block_max(x.m1, &ctrl->red[1], s_red);
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
     if (tid == 0) {
       sc.n_rhs = 1;
       const double d0 = ld_bits(&ctrl->red[0]);
@@ -730,11 +731,11 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
           Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.h0s, sv<KIND>(x, x.iK1, c, li), single);
         put_jv<KIND>(a, 1, x.rb + li, Y, p4.g, single);
       }
-      if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
+      if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       x.m0 = 0.0;
       stage<KIND, ST>(a, x, PH_F1, 1, s_grp);
       block_max(x.m0, &ctrl->red[2], s_red);
-      if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
+      if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       if (tid == 0) {
         sc.n_rhs = 2;
         const double h0 = sc.hs;
@@ -789,18 +790,18 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
       put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
     }
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[1] = globaltimer_ns();
     // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
     if (leader) ctrl->emax[parity ^ 1] = 0ull;
     x.p = p2; x.pn = p3;
     stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[2] = globaltimer_ns();
     // ---- B3: K3 = f(Y3); X' -> j-vector 2
     x.p = p3; x.pn = p4;
     stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
     if (rec) ts[3] = globaltimer_ns();
     // ---- B4: K4 = f(X'); error norm
     if (leader) {
@@ -811,7 +812,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
     x.m1 = 0.0;
     stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
     block_max(x.m1, &ctrl->emax[parity], s_red);
-    if (!sync_all<CTA>(ctrl, bt, a.spin_limit, s_abort)) break;
+    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
     // ---- decision (thread 0; warp 0 runs the learned proposer when installed)
     if (tid == 0) {
       const double E = ld_bits(&ctrl->emax[parity]);
@@ -963,6 +964,8 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   x.gt = group_threads<KIND>(a.rc);
   x.rb = (int)(((long long)b * N) / G);
   x.nr = (int)(((long long)(b + 1) * N) / G) - x.rb;
+  x.rank = b;
+  x.nb = G;
   x.slab = a.slab_bytes > 0 ? dyn : nullptr;
   x.S = (double*)(dyn + a.slab_bytes);
   x.spar = x.S + 6 * d * x.rc;
@@ -1009,7 +1012,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   }
   __syncthreads();
 
-  run_job<KIND, ST, false>(a, x, sc, &s_abort, s_red, s_grp, smlp);
+  run_job<KIND, ST>(a, x, sc, &s_abort, s_red, s_grp, smlp);
 }
 
 }  // namespace bs3
@@ -1017,9 +1020,15 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
 namespace bs3 {
 
 // ---------------------------------------------------------------------------
-// Ragged batches of independent systems: each CTA takes whole systems from a
-// work queue (largest first) and solves them alone, with CTA barriers only;
-// the state lives in global memory (slots [6][d][N] per system).
+// Ragged batches of independent systems in one cooperative launch.  The
+// systems are sorted by decreasing N.  The first n_big of them (too large for
+// one SM's share of the batch) are solved by teams of team CTAs: CTAs
+// [0, n_teams * team) form the teams, each team takes systems from the team
+// queue, splits their rows like the persistent solver and meets at the
+// system's barrier counter.  Every other CTA, and a team CTA once the team
+// queue is empty, takes whole systems from the single queue and solves them
+// alone with CTA barriers.  The state lives in global memory (slots [6][d][N]
+// per system).
 // ---------------------------------------------------------------------------
 struct SysDesc {
   int N, ld;
@@ -1041,76 +1050,118 @@ struct BatchArgs {
   Args common;       // variant, Sigma mode, tolerances, limits
   const SysDesc* sys;
   int S;
-  int* next;         // work-queue counter (zero before the launch)
+  int* next;         // single-queue counter (zero before the launch; systems n_big + next)
+  int n_big;         // systems [0, n_big) go to teams
+  int team;          // CTAs per team (1: no teams)
+  int n_teams;
+  int* big_next;     // team-queue counter (zero before the launch)
+  int* team_job;     // [n_teams] the system a team is on
+  unsigned long long* team_bar;   // [n_teams] team barrier counters (zero before the launch)
+  int* team_status;  // [n_teams] status of a team barrier that ran out (zero before the launch)
 };
+
+// Solves system sidx on the rows [rb, rb + nr) of this CTA, one of nb CTAs.
+template <int KIND, int ST>
+__device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int rank, int nb, Scal& sc, int* s_abort,
+                                          unsigned long long* s_red, unsigned long long* s_grp) {
+  constexpr int d = Dim<KIND>::d;
+  const int tid = threadIdx.x;
+  const SysDesc D = ba.sys[sidx];
+  Args a = ba.common;
+  a.job = JOB_SOLVE;
+  a.N = D.N;
+  a.ld = D.ld;
+  a.q = D.q;
+  a.scale = D.scale;
+  a.rowsum = D.rowsum;
+  a.par = D.par;
+  a.theta_h = D.theta_h;
+  a.X = const_cast<double*>(D.y0);
+  a.jv32 = D.jv32;
+  a.jv64 = D.jv64;
+  a.ctrl = D.ctrl;
+  a.final_y = D.y_final;
+  a.t0 = D.t0;
+  a.t1 = D.t1;
+  a.hmax = 0.1 * (D.t1 - D.t0);
+  a.n_out = 0;
+  a.slab_bytes = 0;
+  a.hist = nullptr;
+  a.mlp = nullptr;
+  a.cancel = nullptr;
+  a.progress = nullptr;
+  Ctx x;
+  x.rank = rank;
+  x.nb = nb;
+  x.rb = (int)(((long long)rank * D.N) / nb);
+  x.nr = (int)(((long long)(rank + 1) * D.N) / nb) - x.rb;
+  a.rc = (D.N + nb - 1) / nb;
+  x.rc = D.N;   // slot stride of the global state; this CTA's rows start at rb
+  x.gt = group_threads<KIND>(a.rc);
+  x.slab = nullptr;
+  x.S = D.state + x.rb;
+  x.spar = const_cast<double*>(D.par) + x.rb;
+  x.srs = const_cast<double*>(D.rowsum) + x.rb;
+  x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum) + x.rb;   // read only by the circadian kind
+  x.sscale = const_cast<float*>(D.scale) + x.rb;
+  x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
+  x.rtol = a.rtol;
+  x.thr = a.atol / a.rtol;
+  x.m0 = 0.0; x.m1 = 0.0;
+  x.c21 = x.c32 = x.hs = x.h0s = 0.0;
+  x.single = (a.variant == V_SINGLE);
+  for (int li = tid; li < x.nr; li += blockDim.x)
+#pragma unroll
+    for (int c = 0; c < d; ++c) {
+      const double y = D.y0[c * D.N + x.rb + li];
+      sv<KIND>(x, x.iX, c, li) = x.single ? (double)(float)y : y;
+    }
+  __syncthreads();
+  run_job<KIND, ST>(a, x, sc, s_abort, s_red, s_grp, nullptr);
+}
 
 template <int KIND, int ST>
 __global__ void __launch_bounds__(kBlock, 1) bs3_batch_kernel(BatchArgs ba) {
-  constexpr int d = Dim<KIND>::d;
   __shared__ int s_abort, s_sys;
   __shared__ unsigned long long s_red[kBlock / 32];
   __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
   __shared__ Scal sc;
   const int tid = threadIdx.x;
+  if (ba.team > 1 && (int)blockIdx.x < ba.n_teams * ba.team) {
+    const int team = blockIdx.x / ba.team, rank = blockIdx.x % ba.team;
+    unsigned long long tt = 0;
+    while (true) {
+      __syncthreads();
+      if (tid == 0) {
+        s_abort = 0;
+        if (rank == 0) {
+          ba.team_job[team] = atomicAdd(ba.big_next, 1);
+          __threadfence();
+        }
+      }
+      // the team agrees on its next system (and, before that, every member
+      // has left the previous one)
+      if (!group_sync(&ba.team_bar[team], &ba.team_status[team], tt, ba.team, ba.common.spin_limit, &s_abort))
+        return;
+      if (tid == 0) s_sys = __ldcg(&ba.team_job[team]);
+      __syncthreads();
+      const int sidx = s_sys;
+      if (sidx >= ba.n_big) break;
+      batch_job<KIND, ST>(ba, sidx, rank, ba.team, sc, &s_abort, s_red, s_grp);
+      if (!group_sync(&ba.team_bar[team], &ba.team_status[team], tt, ba.team, ba.common.spin_limit, &s_abort))
+        return;
+    }
+  }
   while (true) {
     __syncthreads();
     if (tid == 0) {
-      s_sys = atomicAdd(ba.next, 1);
+      s_sys = ba.n_big + atomicAdd(ba.next, 1);
       s_abort = 0;
     }
     __syncthreads();
     const int sidx = s_sys;
     if (sidx >= ba.S) break;
-    const SysDesc D = ba.sys[sidx];
-    Args a = ba.common;
-    a.job = JOB_SOLVE;
-    a.N = D.N;
-    a.ld = D.ld;
-    a.q = D.q;
-    a.scale = D.scale;
-    a.rowsum = D.rowsum;
-    a.par = D.par;
-    a.theta_h = D.theta_h;
-    a.X = const_cast<double*>(D.y0);
-    a.jv32 = D.jv32;
-    a.jv64 = D.jv64;
-    a.ctrl = D.ctrl;
-    a.final_y = D.y_final;
-    a.t0 = D.t0;
-    a.t1 = D.t1;
-    a.hmax = 0.1 * (D.t1 - D.t0);
-    a.n_out = 0;
-    a.rc = D.N;
-    a.slab_bytes = 0;
-    a.hist = nullptr;
-    a.mlp = nullptr;
-    a.cancel = nullptr;
-    a.progress = nullptr;
-    Ctx x;
-    x.rc = D.N;
-    x.gt = group_threads<KIND>(D.N);
-    x.rb = 0;
-    x.nr = D.N;
-    x.slab = nullptr;
-    x.S = D.state;
-    x.spar = const_cast<double*>(D.par);
-    x.srs = const_cast<double*>(D.rowsum);
-    x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum);   // read only by the circadian kind
-    x.sscale = const_cast<float*>(D.scale);
-    x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
-    x.rtol = a.rtol;
-    x.thr = a.atol / a.rtol;
-    x.m0 = 0.0; x.m1 = 0.0;
-    x.c21 = x.c32 = x.hs = x.h0s = 0.0;
-    x.single = (a.variant == V_SINGLE);
-    for (int li = tid; li < D.N; li += blockDim.x)
-#pragma unroll
-      for (int c = 0; c < d; ++c) {
-        const double y = D.y0[c * D.N + li];
-        sv<KIND>(x, x.iX, c, li) = x.single ? (double)(float)y : y;
-      }
-    __syncthreads();
-    run_job<KIND, ST, true>(a, x, sc, &s_abort, s_red, s_grp, nullptr);
+    batch_job<KIND, ST>(ba, sidx, 0, 1, sc, &s_abort, s_red, s_grp);
   }
 }
 
