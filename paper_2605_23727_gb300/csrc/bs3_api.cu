@@ -250,40 +250,43 @@ int pick_grid(bs3_system* s) {
   return BS3_OK;
 }
 
-// Launch plan of a ragged batch (systems sorted by decreasing N).  The cost
-// of a system is N^2 (weight bytes per evaluation); a system above the mean
-// cost per CTA would keep one SM busy long after the others finish, so such
-// systems go to teams of `team` CTAs, team = ceil(largest cost / mean cost)
-// (at most 8, and at least 64 rows per CTA); the teams get the CTAs in
-// proportion to the big systems' share of the cost.
+// Launch plan of a ragged batch (systems sorted by decreasing N).  Cost of a
+// system on one CTA, per attempt: a fixed part (barriers and binary64
+// latency, ~15 us measured) plus three evaluations streaming N^2 weights at
+// the rate one SM reaches (~30 GB/s measured on GB300).  A system above the
+// mean cost per CTA would keep one SM busy long after the others finish, so
+// such systems go to teams of `team` CTAs, team = ceil(largest cost / mean
+// cost) (at most the SM count, and at least 64 rows per CTA); the teams get
+// the CTAs in proportion to the big systems' share of the cost.
 constexpr int kMaxTeams = 256;
+constexpr double kAttemptFixedUs = 15.0;
+constexpr double kCtaStreamBytesPerUs = 30e3;
 
 struct BatchPlan {
   int grid, n_big, team, n_teams;
 };
 
-BatchPlan plan_batch(const std::vector<int64_t>& sortedN, int sms) {
+BatchPlan plan_batch(const std::vector<int64_t>& sortedN, int sms, size_t weight_bytes) {
   const int64_t S = (int64_t)sortedN.size();
   BatchPlan p{(int)std::min<int64_t>(sms, S), 0, 1, 0};
+  auto cost = [&](int64_t n) {
+    return kAttemptFixedUs + 3.0 * (double)n * (double)n * (double)weight_bytes / kCtaStreamBytesPerUs;
+  };
   double total = 0.0;
-  for (int64_t n : sortedN) total += (double)n * (double)n;
+  for (int64_t n : sortedN) total += cost(n);
   if (sms < 4 || S < 1) return p;
   const double share = total / sms;
-  const double big0 = (double)sortedN[0] * (double)sortedN[0];
-  int team = (int)std::ceil(big0 / share);
-  team = std::min<int>(team, 8);
+  int team = (int)std::ceil(cost(sortedN[0]) / share);
+  team = std::min<int>(team, sms);
   team = std::min<int64_t>(team, std::max<int64_t>(1, sortedN[0] / 64));
   if (team < 2) return p;
   int n_big = 0;
   double big = 0.0;
-  while (n_big < S && (double)sortedN[n_big] * (double)sortedN[n_big] > share) {
-    big += (double)sortedN[n_big] * (double)sortedN[n_big];
-    ++n_big;
-  }
+  while (n_big < S && cost(sortedN[n_big]) > share) big += cost(sortedN[n_big++]);
   int ctas = (int)std::lround(sms * big / total);
   ctas = std::max(ctas, team);
   ctas = std::min(ctas, n_big < S ? sms - 1 : sms);
-  int n_teams = std::min<int>(std::min(ctas / team, n_big), kMaxTeams);
+  const int n_teams = std::min<int>(std::min(ctas / team, n_big), kMaxTeams);
   if (n_teams < 1) return p;
   p.grid = sms;
   p.n_big = n_big;
@@ -592,7 +595,7 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
     // (cost ~ N^2: the weight bytes each evaluation streams)
     std::vector<int64_t> sortedN(S);
     for (int64_t k = 0; k < S; ++k) sortedN[k] = Ns[order[k]];
-    const BatchPlan plan = plan_batch(sortedN, sms);
+    const BatchPlan plan = plan_batch(sortedN, sms, eb);
     ba.n_big = plan.n_big;
     ba.team = plan.team;
     ba.n_teams = plan.n_teams;
