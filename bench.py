@@ -67,6 +67,7 @@ CASES = {
     "proposer_lco8192_f16": None,
     "phases_kuramoto4096_mixed1_f32": None,
     "sweep_kuramoto4096": None,
+    "beta_gamma_suite": None,
 }
 
 # FP32 instructions per pair of the circadian coupling (own arctangent): the
@@ -175,6 +176,75 @@ def run_skewed_case(name):
                       "big_alone_ms": e0.elapsed_time(e1), "big_attempts_in_batch": stats[0].n_accepted +
                       stats[0].n_rejected, "big_attempts_alone": st.n_accepted + st.n_rejected,
                       "big_max_abs_diff": float(np.max(np.abs(yf[:2 * 8192] - yo.cpu().numpy())))}))
+
+
+def run_beta_case(name):
+    """The paper's performance parameters (Sec. 2.5, Eq. Beta-2MP and
+    Gamma-2MP) measured on the GPU over a seeded synthetic test suite:
+    beta = steps of Double / steps of the mixed solver (accepted + rejected),
+    gamma = time per step of the mixed solver / of Double, Gamma = gamma / beta
+    = time ratio.  Benchmarks: Benchmark 1 (paper form, heterogeneous M),
+    Kuramoto, circadian; N in {256, 1024}; rtol = atol in {1e-4, 1e-6, 1e-8};
+    seeds 0..3.  Double stores binary64 weights, the other solvers binary32
+    (G = S).  Statistics over the tests every solver finished, as in Table
+    Beta-values: (min, 1st quartile, median, 3rd quartile, max)."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    makers = {
+        "LCO": lambda N, seed: workloads.lco_paper(N, seed, heterogeneous=True),
+        "Kur": lambda N, seed: workloads.kuramoto(N, seed, t1=10.0),
+        "CC": lambda N, seed: workloads.circadian(N, seed, t1=48.0),
+    }
+    solvers = (("single", "f32"), ("mixed1", "f32"), ("mixed2", "f32"), ("double", "f64"))
+    tests = []
+    for bench_name, make in makers.items():
+        for N in (256, 1024):
+            for seed in range(4):
+                w = make(N, seed)
+                systems = {store: bs3.System.from_workload(w, store) for store in ("f32", "f64")}
+                y0 = torch.tensor(w.y0, device="cuda")
+                yo = torch.empty_like(y0)
+                for rt in (1e-4, 1e-6, 1e-8):
+                    rec = {"benchmark": bench_name, "N": N, "seed": seed, "rtol": rt}
+                    for variant, store in solvers:
+                        best, st, rc = None, None, None
+                        for _ in range(2):
+                            e0 = torch.cuda.Event(enable_timing=True)
+                            e1 = torch.cuda.Event(enable_timing=True)
+                            e0.record()
+                            rc, st = bs3.bs3_solve(systems[store].handle, w.t0, w.t1, y0, rt, rt,
+                                                   bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2, None, 0, None, yo, 0)
+                            e1.record()
+                            e1.synchronize()
+                            ms = e0.elapsed_time(e1)
+                            best = ms if best is None else min(best, ms)
+                        rec[variant] = {"ok": rc == bs3.OK, "steps": st.n_accepted + st.n_rejected, "ms": best}
+                    tests.append(rec)
+                    print(json.dumps(rec), flush=True)
+                for sy in systems.values():
+                    sy.close()
+
+    def quant(v):
+        q = np.quantile(np.asarray(v), [0.0, 0.25, 0.5, 0.75, 1.0])
+        return [round(float(x), 3) for x in q]
+
+    summary = {}
+    for bench_name in makers:
+        done = [t for t in tests if t["benchmark"] == bench_name and all(t[v]["ok"] for v, _ in solvers)]
+        row = {"tests_finished_by_all": len(done)}
+        for variant, _ in solvers[:3]:
+            beta = [t["double"]["steps"] / t[variant]["steps"] for t in done]
+            gamma = [(t[variant]["ms"] / t[variant]["steps"]) / (t["double"]["ms"] / t["double"]["steps"])
+                     for t in done]
+            Gam = [t[variant]["ms"] / t["double"]["ms"] for t in done]
+            row[variant] = {"beta": quant(beta), "gamma": quant(gamma), "Gamma": quant(Gam),
+                            "Gamma_below_1": sum(g < 1.0 for g in Gam)}
+        summary[bench_name] = row
+    print(json.dumps({"case": name, "paper_naive_gamma": {"single": 0.5, "mixed1": 0.583, "mixed2": 0.75},
+                      "summary": summary}))
 
 
 def run_proposer_case(name):
@@ -334,6 +404,8 @@ def run_case(name):
         return run_phases_case(name)
     if name.startswith("sweep"):
         return run_sweep_case(name)
+    if name.startswith("beta"):
+        return run_beta_case(name)
     if name.startswith("ragged_skewed"):
         return run_skewed_case(name)
     if name.startswith("ragged"):
