@@ -59,6 +59,7 @@ CASES = {
     "lco16384_mixed1_f16": (lambda: workloads.lco_config(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "f16"),
     "lco32768_mixed1_f16": (lambda: workloads.lco_config(32768, 0, t1=0.2, rtol=RTOL), "mixed1", "f16"),
     "circadian16384_mixed1_bf16": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "bf16"),
+    "circadian16384_mixed1_fp8": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "fp8e4m3"),
     "ensemble256_kuramoto8192": None,
     "ensemble128_kuramoto1024": None,
     "ragged1000_lco_mixed1_f16": None,

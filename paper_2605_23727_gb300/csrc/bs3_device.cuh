@@ -300,4 +300,49 @@ __device__ __forceinline__ float atan_f32(float x) {
   return copysignf(r, x);
 }
 
+// Packed binary32 pairs (Blackwell f32x2 instructions): each lane performs two
+// IEEE operations per instruction, so the results equal the scalar ones.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Two arctangents at once: the same operations as atan_f32 lane by lane
+// (bit-identical results), with the polynomial in packed instructions.
+__device__ __forceinline__ void atan_f32x2(float x0, float x1, float& r0, float& r1) {
+  const float a0 = fabsf(x0), a1 = fabsf(x1);
+  const bool b0 = a0 > 1.0f, b1 = a1 > 1.0f;
+  const unsigned long long t = pk2(b0 ? rcp_approx(a0) : a0, b1 ? rcp_approx(a1) : a1);
+  const unsigned long long z = mul2(t, t);
+  unsigned long long p = pk2(2.849889454e-03f, 2.849889454e-03f);
+  p = fma2(p, z, pk2(-1.606862806e-02f, -1.606862806e-02f));
+  p = fma2(p, z, pk2(4.269151762e-02f, 4.269151762e-02f));
+  p = fma2(p, z, pk2(-7.504294813e-02f, -7.504294813e-02f));
+  p = fma2(p, z, pk2(1.064093411e-01f, 1.064093411e-01f));
+  p = fma2(p, z, pk2(-1.420364380e-01f, -1.420364380e-01f));
+  p = fma2(p, z, pk2(1.999261975e-01f, 1.999261975e-01f));
+  p = fma2(p, z, pk2(-3.333307207e-01f, -3.333307207e-01f));
+  p = fma2(p, z, pk2(1.000000000e+00f, 1.000000000e+00f));
+  float q0, q1;
+  upk2(mul2(t, p), q0, q1);
+  q0 = b0 ? (1.57079637f - q0) : q0;
+  q1 = b1 ? (1.57079637f - q1) : q1;
+  r0 = copysignf(q0, x0);
+  r1 = copysignf(q1, x1);
+}
+
 }  // namespace bs3

@@ -273,8 +273,12 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e)
-          acc[r][0].add_f(L::f(raw[r], e), atan_f32(__fsub_rn(xj[e], xi32[r])));
+        for (int e = 0; e < VEC; e += 2) {
+          float a0, a1;
+          atan_f32x2(__fsub_rn(xj[e], xi32[r]), __fsub_rn(xj[e + 1], xi32[r]), a0, a1);
+          acc[r][0].add_f(L::f(raw[r], e), a0);
+          acc[r][0].add_f(L::f(raw[r], e + 1), a1);
+        }
     } else {
       double xj[VEC];
 #pragma unroll
