@@ -350,11 +350,14 @@ def run_sweep_case(name):
     y0 = torch.tensor(w.y0, device="cuda")
     yo = torch.empty_like(y0)
     rtols = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9]
-    combos = [("double", "f64"), ("mixed2", "f32"), ("mixed1", "f32"), ("single", "f32"),
-              ("mixed2", "bf16"), ("mixed1", "bf16"), ("mixed1", "f16")]
+    combos = [("double", "f64", "bs32"), ("mixed2", "f32", "bs32"), ("mixed1", "f32", "bs32"),
+              ("single", "f32", "bs32"), ("mixed2", "bf16", "bs32"), ("mixed1", "bf16", "bs32"),
+              ("mixed1", "f16", "bs32"), ("double", "f64", "dp54"), ("mixed1", "f32", "dp54"),
+              ("mixed2", "f32", "dp54")]
     curves = {}
-    for variant, store in combos:
+    for variant, store, method in combos:
         s = bs3.System.from_workload(w, store)
+        s.set_method(method)
         pts = []
         for rt in rtols:
             times = []
@@ -368,14 +371,15 @@ def run_sweep_case(name):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
             err = normalized_error(yo.cpu().numpy(), ref, w.N) if rc == bs3.OK else None
-            rec = {"variant": variant, "weights": store, "rtol": rt, "status": bs3.bs3_status_string(rc),
+            rec = {"variant": variant, "weights": store, "method": method, "rtol": rt,
+                   "status": bs3.bs3_status_string(rc),
                    "ms": min(times), "global_error": err, "accepted": st.n_accepted, "rejected": st.n_rejected,
                    "rhs_evals": st.n_rhs_evals}
             print(json.dumps(rec), flush=True)
             if rc == bs3.OK:
                 pts.append((err, min(times)))
         s.close()
-        curves[f"{variant}/{store}"] = pts
+        curves[f"{variant}/{store}" + ("" if method == "bs32" else "/dp54")] = pts
 
     def time_at(pts, e):
         # log-log interpolation between the two points bracketing error e
@@ -701,6 +705,28 @@ def run_gpu(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         assert rc == bs3.OK
 
+    # ------------------------------------- the fifth-order pair (extension)
+    dp54 = {}
+    for variant, store in (("mixed1", "f32"), ("double", "f64")):
+        sd = bs3.System(w.kind, w.N, w.params, None, device=local, stream=stream.cuda_stream)
+        sd.set_coupling(w.coupling, store)
+        sd.set_method("dp54")
+        best, std = None, None
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, std = bs3.bs3_solve(sd.handle, w.t0, w.t1, y0_d, RTOL, RTOL, bs3.VARIANT_IDS[variant],
+                                    bs3.ACCUM_IDS[args.accum], None, 0, None, y_d, 0)
+            e1.record(stream)
+            e1.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        sd.close()
+        dp54[f"{variant}/{store}"] = {"status": bs3.bs3_status_string(rc), "ms": round(best, 3),
+                                      "attempts": std.n_accepted + std.n_rejected,
+                                      "global_error": normalized_error(y_ref, y_d.cpu().numpy(), w.N)}
+
     # --------------------------------------------------------------- roofline
     evals = st.n_rhs_evals
     bytes_per_eval = w.N * w.N * STORE_BYTES[h_store] + w.N * 4 * 2 + n * 8 * 6
@@ -737,6 +763,7 @@ def run_gpu(args):
         "speedup_vs_fp64_gpu": survey["double/f64"]["ms"] / ms,
         "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": evals,
         "survey": survey,
+        "dormand_prince_54": dp54,
         "wall_s_timed_region": wall,
         "clocks": clocks,
         "e2e": {"value": round(statistics.median(e2e_ms), 4), "unit": "ms",

@@ -179,6 +179,26 @@ enum {
     BS3_TUNE_CTAS = 2
 };
 
+/* Embedded Runge-Kutta pair of bs3_solve (bs3_set_method). */
+enum {
+    /* Bogacki-Shampine 3(2), the paper's solver (default). */
+    BS3_METHOD_BS32 = 0,
+    /* Dormand-Prince 5(4), the extension of the precision variants to another
+     * explicit FSAL pair (Sec. 4): seven stages (six evaluations per attempt),
+     * error e = b - b_hat of the published pair in the norm of Eq.
+     * ERROR-O23, controller exponent 1/5, Table MP-Distrib carried stage by
+     * stage (Mixed1: stages 2..6 (S,S,S), stage 7 (D,D,S); Mixed2: all
+     * (D,D,S)).  Dense output stays the cubic Hermite on X^n, K_1, X^{n+1},
+     * K_7. */
+    BS3_METHOD_DP54 = 1
+};
+
+/* Selects the embedded pair of later bs3_solve calls on this system.
+ * bs3_attempt and bs3_batch_solve run Bogacki-Shampine 3(2) only (bs3_attempt
+ * returns BS3_ERR_INVALID_ARG on a Dormand-Prince system).  Errors:
+ * BS3_ERR_INVALID_ARG for an unknown method. */
+int bs3_set_method(bs3_system_t sys, int method);
+
 /* Sets a tuning knob of the system (takes effect at the next launch).
  * Errors: BS3_ERR_INVALID_ARG for an unknown key or value.  The paper has no
  * counterpart (it concerns only how this library maps the method on the GPU). */

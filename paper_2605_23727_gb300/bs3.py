@@ -37,8 +37,10 @@ EXPORTED = (
     "bs3_get_coupling", "bs3_rhs", "bs3_attempt", "bs3_solve", "bs3_destroy_system",
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
-    "bs3_ensemble_solve", "bs3_batch_solve", "bs3_autotune",
+    "bs3_ensemble_solve", "bs3_batch_solve", "bs3_autotune", "bs3_set_method",
 )
+METHOD_BS32, METHOD_DP54 = 0, 1
+METHOD_IDS = {"bs32": METHOD_BS32, "dp54": METHOD_DP54}
 TUNE_CTAS = 2
 MLP_PARAMS = 1313
 MLP_MODEL = 1325
@@ -107,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_solve_noalloc": (I, [I, I64, P, P, P, I, I64, D, D, P, D, D, I, I, P, I64, P, P,
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
+        "bs3_set_method": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -178,6 +181,10 @@ def bs3_solve(sys_: int, t0: float, t1: float, y0, rtol: float, atol: float, var
                           _ptr(y_out), _ptr(final_y), flags, ctypes.byref(st),
                           None if limits is None else ctypes.byref(limits))
     return rc, st
+
+
+def bs3_set_method(sys_: int, method: int) -> int:
+    return load().bs3_set_method(sys_, method)
 
 
 def bs3_set_tuning(sys_: int, key: int, value: int) -> int:
@@ -343,6 +350,11 @@ class System:
         if rc != OK:
             raise RuntimeError(bs3_status_string(rc))
         return q, s
+
+    def set_method(self, method: str) -> None:
+        rc = bs3_set_method(self.handle, METHOD_IDS[method])
+        if rc != OK:
+            raise RuntimeError(bs3_status_string(rc))
 
     def solve(self, t0, t1, y0, rtol, atol, variant="double", accum="float2", t_out=None,
               limits: Optional[bs3_limits] = None):

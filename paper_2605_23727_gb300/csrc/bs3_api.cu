@@ -64,6 +64,7 @@ struct bs3_system {
   bool allow_resident = false;   // see BS3_TUNE_RESIDENT_WEIGHTS
   int l2_keep = 1;
   int tune_ctas = 0;           // 0 = one CTA per SM
+  int method = BS3_METHOD_BS32;
   float* mlp = nullptr;        // learned proposer (kMlpModel binary32, weights bf16-rounded)
   bool mlp_on = false;
   int mlp_off = 0;
@@ -216,6 +217,8 @@ int ensure_stage(double** buf, size_t* cap, size_t n) {
 
 // One CTA per SM (at most one per row block of agents).  Each CTA keeps the
 // state of ceil(N / grid) agents in shared memory.
+int n_slots(int method) { return method == BS3_METHOD_DP54 ? 9 : 6; }
+
 int pick_grid(bs3_system* s) {
   if (s->grid_store == s->store && s->grid > 0) return BS3_OK;
   const void* k = kernel_for(s->kind, s->store);
@@ -225,7 +228,7 @@ int pick_grid(bs3_system* s) {
   const int64_t cap = s->tune_ctas > 0 ? std::min(s->tune_ctas, sms) : sms;
   const int64_t grid = std::min<int64_t>(cap, std::max<int64_t>(1, (s->N + rb - 1) / rb));
   const int rc = (int)((s->N + grid - 1) / grid);
-  const size_t state = (state_smem_bytes(s->d, rc) + 15) / 16 * 16;
+  const size_t state = (state_smem_bytes(s->d, rc, n_slots(s->method)) + 15) / 16 * 16;
   const size_t mlp = s->mlp_on ? (size_t)kMlpModel * sizeof(float) : 0;
   if (state + mlp > (size_t)200 * 1024) return BS3_ERR_INVALID_ARG;
   // keep each CTA's weight rows resident in shared memory when they fit
@@ -318,6 +321,8 @@ void fill_args(const bs3_system* s, Args& a) {
   a.max_rejects = 85000;
   a.rtol = 1.0;
   a.atol = 1.0;
+  a.method = s->method;
+  a.n_slots = n_slots(s->method);
 }
 
 int launch(bs3_system* s, Args& a) {
@@ -580,6 +585,8 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
     a.max_attempts = 100000;
     a.max_rejects = 85000;
     a.l2_keep = 0;
+    a.method = M_BS32;
+    a.n_slots = 6;
     if (kind == BS3_CIRCADIAN)
       for (int q = 0; q < 8; ++q) a.g[q] = params[offP[0] + Ns[0] + q];   // constants shared by the batch
     ba.sys = (const SysDesc*)(arena + oDesc);
@@ -672,6 +679,13 @@ int bs3_set_proposer(bs3_system_t s, const float* model) {
   if (!s->mlp) BS3_CUDA(cudaMalloc(&s->mlp, kMlpModel * sizeof(float)));
   BS3_CUDA(cudaMemcpy(s->mlp, h, kMlpModel * sizeof(float), cudaMemcpyHostToDevice));
   s->mlp_on = true;
+  return BS3_OK;
+}
+
+int bs3_set_method(bs3_system_t s, int method) {
+  if (!s || (method != BS3_METHOD_BS32 && method != BS3_METHOD_DP54)) return BS3_ERR_INVALID_ARG;
+  s->method = method;
+  s->grid_store = -1;   // the state slots change the launch plan
   return BS3_OK;
 }
 
@@ -892,6 +906,7 @@ int bs3_rhs(bs3_system_t s, double t, const double* y, int f_prec, int sigma_pre
 int bs3_attempt(bs3_system_t s, double t, double h, const double* x, const double* k1, double rtol, double atol,
                 int variant, int accum, double* xn_out, double* k4_out, double* err_out) {
   if (!s || !x || !k1 || !xn_out || !k4_out || !err_out || s->store < 0) return BS3_ERR_INVALID_ARG;
+  if (s->method != BS3_METHOD_BS32) return BS3_ERR_INVALID_ARG;   // one attempt: Bogacki-Shampine only
   if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64)
     return BS3_ERR_INVALID_ARG;
   if (!(h > 0.0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;

@@ -103,6 +103,19 @@ __device__ __forceinline__ double cbrt_pos(double q) {
   return fma(-fma(y * y, y, -q), r, y);
 }
 
+// q^(1/5) for the controller of the fifth-order pair, q > 0: a binary32 seed
+// (log2/exp2) refined by one Newton step y - (y^5 - q) / (5 y^4) in binary64
+// with a binary32 estimate of 1 / (5 y^4) (relative error ~1e-14).  Clamped
+// like cbrt_pos; outside [0.095, 9537] the controller's limits decide.
+__device__ __forceinline__ double root5_pos(double q) {
+  q = fmin(fmax(q, 1e-30), 1e30);
+  const float yf = exp2f(0.2f * log2f((float)q));
+  const double y = (double)yf;
+  const double y2 = y * y, y4 = y2 * y2;
+  const double r = (double)(1.0f / (5.0f * (float)y4));
+  return fma(-fma(y4, y, -q), r, y);
+}
+
 // Grid barrier for a cooperative launch.  Every CTA adds one arrival to a
 // monotonic counter (release) and polls it until it reaches its target.  The
 // wait is bounded by spin_limit polls; a CTA that gives up sets the status to

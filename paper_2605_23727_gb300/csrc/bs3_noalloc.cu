@@ -188,6 +188,8 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   a.spin_limit = (long long)1 << 26;
   a.rc = rcap;
   a.slab_bytes = resident ? (int)slab : 0;
+  a.method = M_BS32;
+  a.n_slots = 6;
   int l2 = 0;
   NA_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device));
   a.l2_keep = ((double)N * ld * (store == BS3_F64 ? 8 : 4) <= 0.6 * (double)l2) ? 1 : 0;

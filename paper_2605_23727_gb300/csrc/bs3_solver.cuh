@@ -56,7 +56,11 @@ struct Args {
   long long hist_cap;
   const float* mlp;         // optional learned proposer: kMlpModel binary32 (bf16-rounded weights)
   int smem_mlp_off;         // byte offset of its shared-memory copy in the dynamic region
+  int method;               // M_BS32 (Bogacki-Shampine 3(2)) or M_DP54 (Dormand-Prince 5(4))
+  int n_slots;              // state slots per agent: 6 (BS3) or 9 (DP5)
 };
+
+enum Method { M_BS32 = 0, M_DP54 = 1 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -72,6 +76,31 @@ struct Prec {
 __device__ __forceinline__ Prec variant_prec(int v, int stage) {
   if (v == V_SINGLE) return Prec{0, 0, 0};
   if (v == V_MIXED1) return stage == 4 ? Prec{1, 1, 0} : Prec{0, 0, 0};
+  if (v == V_MIXED2) return Prec{1, 1, 0};
+  return Prec{1, 1, 1};
+}
+
+// Dormand-Prince 5(4) (the embedded pair of the extension to other explicit
+// schemes, Sec. 4): a_lm (l = 2..7, m = 1..l-1; row 7 = b, the FSAL row) and
+// e = b - b_hat, each the binary64 rounding of the published rational.
+static __constant__ double kDpA[8][8] = {
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 1.0 / 5.0, 0, 0, 0, 0, 0, 0},
+    {0, 3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0, 0},
+    {0, 44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0, 0},
+    {0, 19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0, 0},
+    {0, 9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0, 0},
+    {0, 35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0, 0},
+};
+static __constant__ double kDpE[8] = {0, 71.0 / 57600.0, 0.0, -71.0 / 16695.0, 71.0 / 1920.0,
+                                      -17253.0 / 339200.0, 22.0 / 525.0, -1.0 / 40.0};
+
+// Table MP-Distrib carried to the seven stages: Mixed1 keeps every stage in
+// binary32 except the last (FSAL) one, Mixed2 has F and Sigma in binary64.
+__device__ __forceinline__ Prec variant_prec_dp(int v, int stage) {
+  if (v == V_SINGLE) return Prec{0, 0, 0};
+  if (v == V_MIXED1) return stage == 7 ? Prec{1, 1, 0} : Prec{0, 0, 0};
   if (v == V_MIXED2) return Prec{1, 1, 0};
   return Prec{1, 1, 1};
 }
@@ -402,7 +431,8 @@ __device__ __forceinline__ void finish(const Args& a, const RowPar& rp, const do
 // of the CTA's agents lives in shared memory: six slots [d][rc] whose roles
 // (X, X', K1..K4) rotate on accepted steps.
 // ---------------------------------------------------------------------------
-enum Phase { PH_RHS = 0, PH_K1 = 1, PH_F1 = 2, PH_B2 = 3, PH_B3 = 4, PH_B4 = 5 };
+enum Phase { PH_RHS = 0, PH_K1 = 1, PH_F1 = 2, PH_B2 = 3, PH_B3 = 4, PH_B4 = 5, PH_D2 = 6 };
+// Dormand-Prince stage l (2..7) is phase PH_D2 + l - 2.
 
 struct Ctx {
   const unsigned char* slab;  // shared-memory copy of this CTA's weight rows (or null)
@@ -415,6 +445,7 @@ struct Ctx {
   int rc, rb, nr;
   int rank, nb;      // this CTA's place in the group of CTAs that solves the system (nb = 1: alone)
   int iX, iXn, iK1, iK2, iK3, iK4;
+  int iK7;           // Dormand-Prince: slot of K_7 (K_1 in iK1, K_2..K_6 fixed in slots 3..7)
   double c21, c32, hs, h0s, thr, rtol;
   Prec p;    // precision of the stage being evaluated
   Prec pn;   // G precision of the next j-vector
@@ -440,9 +471,104 @@ __device__ __forceinline__ double& sv(const Ctx& x, int slot, int c, int li) {
   return x.S[(slot * Dim<KIND>::d + c) * x.rc + li];
 }
 
+// Slot of Dormand-Prince stage value K_m: K_1 and K_7 swap on accepted steps
+// (FSAL), K_2..K_6 stay in slots 3..7.
+__device__ __forceinline__ int dp_slot(const Ctx& x, int m) {
+  return m == 1 ? x.iK1 : (m == 7 ? x.iK7 : m + 1);
+}
+
+// Dormand-Prince stage argument Y_l = X + h (sum_{m<l} a_lm K_m), the sum
+// over the nonzero a_lm in increasing m, in the state precision.
+template <int KIND>
+__device__ __forceinline__ double dp_arg(const Ctx& x, int l, int c, int li) {
+  const double xo = sv<KIND>(x, x.iX, c, li);
+  if (x.single) {
+    float acc = 0.f;
+    bool first = true;
+    for (int m = 1; m < l; ++m) {
+      const double am = kDpA[l][m];
+      if (am == 0.0) continue;
+      const float term = (float)am * (float)sv<KIND>(x, dp_slot(x, m), c, li);
+      acc = first ? term : acc + term;
+      first = false;
+    }
+    return (double)((float)xo + (float)x.hs * acc);
+  }
+  double acc = 0.0;
+  bool first = true;
+  for (int m = 1; m < l; ++m) {
+    const double am = kDpA[l][m];
+    if (am == 0.0) continue;
+    const double term = am * sv<KIND>(x, dp_slot(x, m), c, li);
+    acc = first ? term : acc + term;
+    first = false;
+  }
+  return xo + x.hs * acc;
+}
+
+// Epilogue of Dormand-Prince stage l: K_l, then the next stage argument and
+// its j-vector (Y_7 = X'), or after the last stage the error of Eq. ERROR-O23
+// with e = b - b_hat.
+template <int KIND>
+__device__ __forceinline__ void epilogue_dp(const Args& a, Ctx& x, int l, int li, double s0, double s1) {
+  constexpr int d = Dim<KIND>::d;
+  const int i = x.rb + li;
+  const RowPar rp{x.sscale[li], x.spar[li], x.sth[li], x.srs[li]};
+  double Y[d], K[d];
+#pragma unroll
+  for (int c = 0; c < d; ++c) Y[c] = (l == 7) ? sv<KIND>(x, x.iXn, c, li) : dp_arg<KIND>(x, l, c, li);
+  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K);
+#pragma unroll
+  for (int c = 0; c < d; ++c) sv<KIND>(x, dp_slot(x, l), c, li) = K[c];
+  if (l < 7) {
+#pragma unroll
+    for (int c = 0; c < d; ++c) {
+      Y[c] = dp_arg<KIND>(x, l + 1, c, li);
+      if (l + 1 == 7) sv<KIND>(x, x.iXn, c, li) = Y[c];
+    }
+    put_jv<KIND>(a, (l + 1) & 1, i, Y, x.pn.g, x.single);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < d; ++c) {
+    double dv;
+    if (x.single) {
+      float acc = 0.f;
+      bool first = true;
+      for (int m = 1; m <= 7; ++m) {
+        const double em = kDpE[m];
+        if (em == 0.0) continue;
+        const float term = (float)em * (float)sv<KIND>(x, dp_slot(x, m), c, li);
+        acc = first ? term : acc + term;
+        first = false;
+      }
+      dv = (double)((float)x.hs * acc);
+    } else {
+      double acc = 0.0;
+      bool first = true;
+      for (int m = 1; m <= 7; ++m) {
+        const double em = kDpE[m];
+        if (em == 0.0) continue;
+        const double term = em * sv<KIND>(x, dp_slot(x, m), c, li);
+        acc = first ? term : acc + term;
+        first = false;
+      }
+      dv = x.hs * acc;
+    }
+    const double w = fmax(fmax(fabs(sv<KIND>(x, x.iX, c, li)), fabs(Y[c])), x.thr);
+    double v = fabs(dv) / w;
+    if (!isfinite(Y[c]) || !isfinite(K[c])) v = nan_d();
+    x.m1 = max_nan(x.m1, v);
+  }
+}
+
 template <int KIND>
 __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int li, double s0, double s1) {
   constexpr int d = Dim<KIND>::d;
+  if (phase >= PH_D2) {
+    epilogue_dp<KIND>(a, x, phase - PH_D2 + 2, li, s0, s1);
+    return;
+  }
   const int N = a.N;
   const int i = x.rb + li;
   const RowPar rp{x.sscale[li], x.spar[li], x.sth[li], x.srs[li]};
@@ -614,10 +740,11 @@ __device__ __forceinline__ double ld_bits(const unsigned long long* p) {
   return __longlong_as_double((long long)__ldcg(p));
 }
 
-// Shared-memory bytes of a launch: six state slots [d][rc] plus per-agent
+// Shared-memory bytes of a launch: the state slots [slots][d][rc] (six for
+// Bogacki-Shampine, nine for Dormand-Prince) plus per-agent
 // parameters (three binary64 and one binary32 per agent).
-__host__ __device__ constexpr size_t state_smem_bytes(int d, int rc) {
-  return (size_t)rc * (6 * d * 8 + 3 * 8 + 4) + 16;
+__host__ __device__ constexpr size_t state_smem_bytes(int d, int rc, int slots = 6) {
+  return (size_t)rc * (slots * d * 8 + 3 * 8 + 4) + 16;
 }
 
 
@@ -686,6 +813,8 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
   const Prec p2 = variant_prec(a.variant, 2);
   const Prec p3 = variant_prec(a.variant, 3);
   const Prec p4 = variant_prec(a.variant, 4);
+  const bool dp = (a.method == M_DP54);
+  const Prec plast = dp ? variant_prec_dp(a.variant, 7) : p4;   // row of the first K1 and the starting step
   const double rtol = a.rtol;
 
   if (tid == 0) {
@@ -702,14 +831,14 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       double Y[d];
 #pragma unroll
       for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
-      put_jv<KIND>(a, 0, x.rb + li, Y, p4.g, single);
+      put_jv<KIND>(a, 0, x.rb + li, Y, plast.g, single);
     }
   }
   if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
 
   if (a.job == JOB_SOLVE) {
-    // ---- K1 = f(t0, y0) with the k4 row; starting-step norms d0, d1
-    x.p = p4;
+    // ---- K1 = f(t0, y0) with the last stage's row; starting-step norms d0, d1
+    x.p = plast;
     x.m0 = 0.0; x.m1 = 0.0;
     stage<KIND, ST>(a, x, PH_K1, 0, s_grp);
     block_max(x.m0, &ctrl->red[0], s_red);
@@ -733,7 +862,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
 #pragma unroll
         for (int c = 0; c < d; ++c)
           Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.h0s, sv<KIND>(x, x.iK1, c, li), single);
-        put_jv<KIND>(a, 1, x.rb + li, Y, p4.g, single);
+        put_jv<KIND>(a, 1, x.rb + li, Y, plast.g, single);
       }
       if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       x.m0 = 0.0;
@@ -746,7 +875,8 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         const double d1 = ld_bits(&ctrl->red[1]);
         const double d2 = ld_bits(&ctrl->red[2]) / h0;
         const double m = fmax(d1, d2);
-        const double h1 = (m > 1e-15) ? pow(0.01 / m, 1.0 / 3.0) : fmax(1e-6, h0 * 1e-3);
+        // exponent 1/(q+1), q the order of the embedded solution
+        const double h1 = (m > 1e-15) ? pow(0.01 / m, dp ? 0.2 : 1.0 / 3.0) : fmax(1e-6, h0 * 1e-3);
         sc.h = fmin(fmin(100.0 * h0, h1), a.hmax);
       }
     }
@@ -787,41 +917,74 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
     x.c21 = sc.c21;
     x.c32 = sc.c32;
     const int parity = sc.parity;
-    for (int li = tid; li < x.nr; li += blockDim.x) {
-      double Y[d];
+    bool aborted = false;
+    if (dp) {
+      // ---- Dormand-Prince: A: Y2 -> j-vector 0; stage l reads the j-vector
+      // of Y_l (buffer l % 2) and writes that of Y_{l+1}
+      for (int li = tid; li < x.nr; li += blockDim.x) {
+        double Y[d];
 #pragma unroll
-      for (int c = 0; c < d; ++c)
-        Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
-      put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
+        for (int c = 0; c < d; ++c) Y[c] = dp_arg<KIND>(x, 2, c, li);
+        put_jv<KIND>(a, 0, x.rb + li, Y, variant_prec_dp(a.variant, 2).g, single);
+      }
+      if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
+      if (rec) ts[1] = globaltimer_ns();
+      if (leader) ctrl->emax[parity ^ 1] = 0ull;
+      for (int l = 2; l <= 7; ++l) {
+        x.p = variant_prec_dp(a.variant, l);
+        x.pn = variant_prec_dp(a.variant, l < 7 ? l + 1 : 7);
+        if (l == 7) {
+          if (leader) {
+            ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
+            if (a.progress) *a.progress = sc.t;
+          }
+          x.m1 = 0.0;
+        }
+        stage<KIND, ST>(a, x, PH_D2 + l - 2, l & 1, s_grp);
+        if (l == 7) block_max(x.m1, &ctrl->emax[parity], s_red);
+        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (rec && (l == 3 || l == 5)) ts[l == 3 ? 2 : 3] = globaltimer_ns();
+      }
+    } else {
+      do {
+        for (int li = tid; li < x.nr; li += blockDim.x) {
+          double Y[d];
+#pragma unroll
+          for (int c = 0; c < d; ++c)
+            Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
+          put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
+        }
+        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (rec) ts[1] = globaltimer_ns();
+        // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
+        if (leader) ctrl->emax[parity ^ 1] = 0ull;
+        x.p = p2; x.pn = p3;
+        stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
+        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (rec) ts[2] = globaltimer_ns();
+        // ---- B3: K3 = f(Y3); X' -> j-vector 2
+        x.p = p3; x.pn = p4;
+        stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
+        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (rec) ts[3] = globaltimer_ns();
+        // ---- B4: K4 = f(X'); error norm
+        if (leader) {
+          ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
+          if (a.progress) *a.progress = sc.t;
+        }
+        x.p = p4;
+        x.m1 = 0.0;
+        stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
+        block_max(x.m1, &ctrl->emax[parity], s_red);
+        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+      } while (false);
     }
-    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
-    if (rec) ts[1] = globaltimer_ns();
-    // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
-    if (leader) ctrl->emax[parity ^ 1] = 0ull;
-    x.p = p2; x.pn = p3;
-    stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
-    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
-    if (rec) ts[2] = globaltimer_ns();
-    // ---- B3: K3 = f(Y3); X' -> j-vector 2
-    x.p = p3; x.pn = p4;
-    stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
-    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
-    if (rec) ts[3] = globaltimer_ns();
-    // ---- B4: K4 = f(X'); error norm
-    if (leader) {
-      ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
-      if (a.progress) *a.progress = sc.t;
-    }
-    x.p = p4;
-    x.m1 = 0.0;
-    stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
-    block_max(x.m1, &ctrl->emax[parity], s_red);
-    if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
+    if (aborted) break;
     // ---- decision (thread 0; warp 0 runs the learned proposer when installed)
     if (tid == 0) {
       const double E = ld_bits(&ctrl->emax[parity]);
       sc.E = E;
-      sc.n_rhs += 3;
+      sc.n_rhs += dp ? 6 : 3;
       if (rec) {
         ts[4] = globaltimer_ns();
         double* r = a.hist + (size_t)(sc.n_acc + sc.n_rej) * kHistDoubles;
@@ -845,7 +1008,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
           ++e;
         }
         sc.out_end = e;
-        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * cbrt_pos(rtol / E));
+        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * (dp ? root5_pos(rtol / E) : cbrt_pos(rtol / E)));
         if (sc.rejected) fac = fmin(1.0, fac);
         sc.h = h * fac;
         sc.t = t_new;
@@ -867,7 +1030,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         sc.accepted = 1;
       } else {
         ++sc.n_rej;
-        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * cbrt_pos(rtol / E));
+        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * (dp ? root5_pos(rtol / E) : cbrt_pos(rtol / E)));
         sc.rejected = 1;
         sc.mlp_go = 0;
       }
@@ -905,7 +1068,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
 #pragma unroll
             for (int c = 0; c < d; ++c) {
               const double y0 = sv<KIND>(x, x.iX, c, li), y1 = sv<KIND>(x, x.iXn, c, li);
-              const double f0 = sv<KIND>(x, x.iK1, c, li), f1 = sv<KIND>(x, x.iK4, c, li);
+              const double f0 = sv<KIND>(x, x.iK1, c, li), f1 = sv<KIND>(x, dp ? x.iK7 : x.iK4, c, li);
               a.y_out[(size_t)k * d * N + c * N + x.rb + li] =
                   ((1.0 - th) * y0 + th * y1) +
                   (th * (th - 1.0)) * (((1.0 - 2.0 * th) * (y1 - y0) + ((th - 1.0) * hstep) * f0) + (th * hstep) * f1);
@@ -927,7 +1090,11 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         __syncthreads();
       }
       int tmp = x.iX; x.iX = x.iXn; x.iXn = tmp;
-      tmp = x.iK1; x.iK1 = x.iK4; x.iK4 = tmp;
+      if (dp) {
+        tmp = x.iK1; x.iK1 = x.iK7; x.iK7 = tmp;
+      } else {
+        tmp = x.iK1; x.iK1 = x.iK4; x.iK4 = tmp;
+      }
     }
   }
 
@@ -972,11 +1139,12 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   x.nb = G;
   x.slab = a.slab_bytes > 0 ? dyn : nullptr;
   x.S = (double*)(dyn + a.slab_bytes);
-  x.spar = x.S + 6 * d * x.rc;
+  x.spar = x.S + a.n_slots * d * x.rc;
   x.sth = x.spar + x.rc;
   x.srs = x.sth + x.rc;
   x.sscale = (float*)(x.srs + x.rc);
   x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
+  x.iK7 = 8;   // Dormand-Prince: K_l in slot l + 1 (nine slots)
   x.rtol = a.rtol;
   x.thr = a.atol / a.rtol;
   x.m0 = 0.0; x.m1 = 0.0;
