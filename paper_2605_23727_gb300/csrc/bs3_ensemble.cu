@@ -16,7 +16,8 @@
 // first).  The binary32 sine and cosine of every stage argument are kept
 // ([T][N] pairs) for the i-side finish of the next product, so the epilogue
 // does not reduce the phase again: binary64 arithmetic is scarce on GB300 and
-// the epilogue, not the tensor cores, bounds a stage.
+// the epilogue, not the tensor cores, bounds a stage (for the same reason the
+// binary64 stage combinations use fused multiply-adds).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -76,9 +77,17 @@ __device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
   a.Vl[rc] = __float2bfloat16_rn(c - __bfloat162float(ch));
 }
 
+// Integer tests on the exponent field (binary64 compares issue at the binary64
+// rate on GB300): not finite = exponent all ones; NaN = that and a nonzero
+// fraction.
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned)__double2hiint(v) & 0x7ff00000u) != 0x7ff00000u;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
-  unsigned long long x = (unsigned long long)__double_as_longlong(fabs(v));
-  if (v != v) x = 0x7ff8000000000000ull;
+  // |v| as bits; NaN keeps its (above +Inf) bits, canonicalised
+  unsigned long long x = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  if (x > 0x7ff0000000000000ull) x = 0x7ff8000000000000ull;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, x, off);
@@ -91,8 +100,9 @@ __device__ __forceinline__ double warp_max(double v) {
 // Newton step in binary64 (relative error ~1e-14; three binary64 operations
 // instead of a correctly rounded division).  Outside [1e-30, 1e30] it divides.
 __device__ __forceinline__ double ratio(double n, double d) {
-  if (!(d >= 1e-30 && d <= 1e30)) return n / d;
-  const double r0 = (double)__frcp_rn((float)d);
+  const float df = (float)d;
+  if (!(df >= 1e-30f && df <= 1e30f)) return n / d;   // (the range test in binary32)
+  const double r0 = (double)__frcp_rn(df);
   return n * (r0 * fma(-d, r0, 2.0));
 }
 
@@ -152,18 +162,18 @@ struct Epilogue {
           if (lane == 0) atomicMax(&a.tr.red2[b], (unsigned long long)__double_as_longlong(m));
         } else if (PH == E_B2) {
           a.K2[o] = k;
-          put_v(a, b, i, x[g] + a.tr.c32[b] * k);
+          put_v(a, b, i, fma(a.tr.c32[b], k, x[g]));
         } else if (PH == E_B3) {
           a.K3[o] = k;
-          const double xn = x[g] + a.tr.hs[b] * ((kB1 * k1[g] + kB2 * k2[g]) + kB3 * k);
+          const double xn = fma(a.tr.hs[b], fma(kB3, k, fma(kB2, k2[g], kB1 * k1[g])), x[g]);
           a.X[(1 - xs[g]) * slot + o] = xn;
           put_v(a, b, i, xn);
         } else {
           a.K14[(1 - ks[g]) * slot + o] = k;
-          const double dv = a.tr.hs[b] * (((kE1 * k1[g] + kE2 * k2[g]) + kE3 * k3[g]) + kE4 * k);
+          const double dv = a.tr.hs[b] * fma(kE4, k, fma(kE3, k3[g], fma(kE2, k2[g], kE1 * k1[g])));
           const double w = fmax(fmax(fabs(x[g]), fabs(y[g])), thr);
           double e = ratio(fabs(dv), w);
-          if (!isfinite(y[g]) || !isfinite(k)) e = __longlong_as_double(0x7ff8000000000000ll);
+          if (!finite_bits(y[g]) || !finite_bits(k)) e = __longlong_as_double(0x7ff8000000000000ll);
           const double m = warp_max(e);
           if (lane == 0) atomicMax(&a.tr.emax[b], (unsigned long long)__double_as_longlong(m));
         }
@@ -194,7 +204,7 @@ __global__ void ens_prologue(EArgs a, int which) {
     const double x = a.X[a.tr.xsel[b] * slot + e];
     const double k1 = a.K14[a.tr.ksel[b] * slot + e];
     const double c = which == 0 ? 0.0 : (which == 1 ? a.tr.h0[b] : a.tr.c21[b]);
-    put_v(a, b, i, which == 0 ? x : x + c * k1);
+    put_v(a, b, i, which == 0 ? x : fma(c, k1, x));
   }
 }
 
