@@ -62,6 +62,7 @@ CASES = {
     "circadian16384_mixed1_fp8": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "fp8e4m3"),
     "ensemble256_kuramoto8192": None,
     "ensemble128_kuramoto1024": None,
+    "ensemble128_kuramoto8192": None,
     "ragged1000_lco_mixed1_f16": None,
     "ragged_skewed_lco_f16": None,
     "proposer_lco32768_f16": None,
@@ -87,17 +88,23 @@ def run_ensemble_case(name):
     import __graft_entry__
     __graft_entry__.build()
     bs3.load()
-    T, N, t1 = {"ensemble256_kuramoto8192": (256, 8192, T1), "ensemble128_kuramoto1024": (128, 1024, 10.0)}[name]
+    T, N, t1 = {"ensemble256_kuramoto8192": (256, 8192, T1), "ensemble128_kuramoto8192": (128, 8192, T1),
+                "ensemble128_kuramoto1024": (128, 1024, 10.0)}[name]
     K, omega, theta0 = workloads.kuramoto_ensemble(T=T, N=N, seed=0)
     Kd = torch.tensor(K, dtype=torch.float32, device="cuda")
     om = torch.tensor(omega, dtype=torch.float64, device="cuda")
     th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
     out = torch.empty_like(th)
+    # tile width by the autotuner (bounded solves of each width)
+    rc, tile, us_tile = bs3.bs3_ensemble_autotune(Kd, N, T, om, th, 0.0, t1, RTOL, RTOL, 16, out)
+    if rc != bs3.OK:
+        raise RuntimeError(bs3.bs3_status_string(rc))
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    rc, n_acc, n_rej, status, steps = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, RTOL, RTOL, out)
+    rc, n_acc, n_rej, status, steps = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, RTOL, RTOL, out,
+                                                             tile_n=tile)
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1)
@@ -105,7 +112,8 @@ def run_ensemble_case(name):
     print(json.dumps({"case": name, "status": bs3.bs3_status_string(rc), "ms": ms, "T": T, "N": N,
                       "lockstep_attempts": steps, "attempts_max": int((n_acc + n_rej).max()),
                       "attempts_mean": float((n_acc + n_rej).mean()), "all_ok": bool((status == 0).all()),
-                      "tensor_tflops": flops / (ms * 1e-3) / 1e12,
+                      "tensor_tflops": flops / (ms * 1e-3) / 1e12, "tile_n": tile,
+                      "autotune_us_per_attempt": us_tile,
                       "ms_per_trajectory": ms / T}))
     if rc != bs3.OK:
         sys.exit(1)

@@ -287,7 +287,8 @@ int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B
  * Sigma = binary32 accumulation and i-side finish, F and the state, stage
  * combinations and error norm in binary64 (the oracle's "tensor" variant).
  * K: device, N x N binary32 row-major; omega, theta0, theta_out: device,
- * [T][N] binary64 (trajectory-major).  N % 128 == 0, T % 128 == 0.
+ * [T][N] binary64 (trajectory-major).  N % 128 == 0, T % 64 == 0 (the tile
+ * width is chosen as bs3_ensemble_solve_tiled with tile_n = 0 does).
  * n_acc, n_rej, status (host arrays of T, may be NULL) receive each
  * trajectory's counts and status; *lockstep_attempts (host, may be NULL) the
  * number of lock-step attempts run.  Waits for completion.  Returns
@@ -295,6 +296,29 @@ int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B
 int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
                        double t0, double t1, double rtol, double atol, double* theta_out, int64_t* n_acc,
                        int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream);
+
+/* bs3_ensemble_solve with an explicit output tile width and an optional bound.
+ * tile_n: 256 (128 x 256 accumulator tiles, 128 trajectories per tile; needs
+ * T % 128 == 0), 128 (128 x 128 tiles, 64 trajectories; T % 64 == 0), or 0:
+ * 128 when the 256-wide tiles would fill fewer than 3/4 of the SMs (or T is
+ * not a multiple of 128), else 256.  max_lockstep > 0 stops after that many
+ * lock-step attempts (rounded up to the 8 of one graph launch) and returns
+ * BS3_ERR_MAX_STEPS if trajectories are still running; 0 = no bound beyond
+ * the per-trajectory limits.  The paper has no counterpart. */
+int bs3_ensemble_solve_tiled(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                             double t0, double t1, double rtol, double atol, int tile_n, int64_t max_lockstep,
+                             double* theta_out, int64_t* n_acc, int64_t* n_rej, int32_t* status,
+                             int64_t* lockstep_attempts, void* stream);
+
+/* Autotuner of the ensemble's tile width: runs bounded solves (lockstep_attempts
+ * lock-step attempts, >= 8) with each valid width and returns the one with the
+ * shortest device time per attempt in *tile_out (and that time in
+ * microseconds in *us_out, may be NULL).  scratch_theta: device [T][N]
+ * binary64 buffer the bounded solves write.  Arguments otherwise as
+ * bs3_ensemble_solve.  The paper has no counterpart. */
+int bs3_ensemble_autotune(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                          double t0, double t1, double rtol, double atol, int64_t lockstep_attempts,
+                          double* scratch_theta, int* tile_out, double* us_out);
 
 /* Ragged batch of S independent systems of one kind (sizes N_k may all
  * differ) solved in one launch (the build's batched extension): each CTA takes

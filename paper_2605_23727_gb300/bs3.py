@@ -38,6 +38,7 @@ EXPORTED = (
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
     "bs3_ensemble_solve", "bs3_batch_solve", "bs3_autotune", "bs3_set_method",
+    "bs3_ensemble_solve_tiled", "bs3_ensemble_autotune",
 )
 METHOD_BS32, METHOD_DP54 = 0, 1
 METHOD_IDS = {"bs32": METHOD_BS32, "dp54": METHOD_DP54}
@@ -110,6 +111,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                   ctypes.POINTER(bs3_stats), P]),
         "bs3_get_history": (I, [P, P, ctypes.POINTER(I64)]),
         "bs3_set_method": (I, [P, I]),
+        "bs3_ensemble_solve_tiled": (I, [P, I64, I64, P, P, D, D, D, D, I, I64, P, P, P, P, ctypes.POINTER(I64), P]),
+        "bs3_ensemble_autotune": (I, [P, I64, I64, P, P, D, D, D, D, I64, P, ctypes.POINTER(I),
+                                      ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,15 +262,26 @@ def bs3_tc_gemm(M: int, Nc: int, K: int, A, B, C) -> int:
 
 
 def bs3_ensemble_solve(K, N: int, T: int, omega, theta0, t0: float, t1: float, rtol: float, atol: float,
-                       theta_out, stream: int = 0):
+                       theta_out, stream: int = 0, tile_n: int = 0, max_lockstep: int = 0):
     """Returns (rc, n_acc[T], n_rej[T], status[T], lockstep_attempts)."""
     n_acc = np.zeros(T, dtype=np.int64)
     n_rej = np.zeros(T, dtype=np.int64)
     status = np.zeros(T, dtype=np.int32)
     steps = ctypes.c_int64()
-    rc = load().bs3_ensemble_solve(_ptr(K), N, T, _ptr(omega), _ptr(theta0), t0, t1, rtol, atol, _ptr(theta_out),
-                                   _ptr(n_acc), _ptr(n_rej), _ptr(status), ctypes.byref(steps), stream or None)
+    rc = load().bs3_ensemble_solve_tiled(_ptr(K), N, T, _ptr(omega), _ptr(theta0), t0, t1, rtol, atol, tile_n,
+                                         max_lockstep, _ptr(theta_out), _ptr(n_acc), _ptr(n_rej), _ptr(status),
+                                         ctypes.byref(steps), stream or None)
     return rc, n_acc, n_rej, status, steps.value
+
+
+def bs3_ensemble_autotune(K, N: int, T: int, omega, theta0, t0: float, t1: float, rtol: float, atol: float,
+                          lockstep_attempts: int, scratch_theta):
+    """Returns (rc, tile width, microseconds per lock-step attempt)."""
+    tile = ctypes.c_int()
+    us = ctypes.c_double()
+    rc = load().bs3_ensemble_autotune(_ptr(K), N, T, _ptr(omega), _ptr(theta0), t0, t1, rtol, atol,
+                                      lockstep_attempts, _ptr(scratch_theta), ctypes.byref(tile), ctypes.byref(us))
+    return rc, tile.value, us.value
 
 
 def bs3_batch_solve(kind: int, Ns, params, K, store: int, y0, t0, t1, rtol: float, atol: float, variant: int,

@@ -185,13 +185,13 @@ struct Epilogue {
 constexpr int kEpiWarps = 16;
 constexpr int kEnsThreads = tc::threads_for(kEpiWarps);
 
-template <int PH>
+template <int PH, int BNT>
 __global__ void __launch_bounds__(kEnsThreads, 1)
     ens_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, EArgs a, int K,
                     int* err, long long spin) {
   const Epilogue<PH> epi{a};
-  tc::gemm_tile<kEpiWarps>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, epi, err, spin);
+  tc::gemm_tile<kEpiWarps, BNT>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * BNT, K, epi, err, spin);
 }
 
 // j-vector operand of the stage argument Y = X + c K1 (c = 0, h0 or h/2).
@@ -309,12 +309,14 @@ using namespace bs3::ens;
     if (rc != BS3_OK) goto done;   \
   } while (0)
 
-extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
-                                  double t0, double t1, double rtol, double atol, double* theta_out,
-                                  int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
-                                  void* stream_) {
+template <int BNT>
+int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                        double t0, double t1, double rtol, double atol, int64_t max_lockstep, double* theta_out,
+                        int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
+                        void* stream_, float* loop_ms = nullptr) {
   if (!K || !omega || !theta0 || !theta_out) return BS3_ERR_INVALID_ARG;
-  if (N < tc::BM || N % tc::BM || N % tc::BK || T < tc::BN / 2 || (2 * T) % tc::BN) return BS3_ERR_INVALID_ARG;
+  using TL = tc::Tile<BNT>;
+  if (N < tc::BM || N % tc::BM || N % tc::BK || T < BNT / 2 || (2 * T) % BNT) return BS3_ERR_INVALID_ARG;
   if (N > (1 << 20) || T > (1 << 16)) return BS3_ERR_INVALID_ARG;
   if (!(t1 > t0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream_;
@@ -328,13 +330,14 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   unsigned long long* usc = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   CUtensorMap mAh, mAl, mBh, mBl, mBh1, mBl1;
   EArgs a;
   std::memset(&a, 0, sizeof(a));
   int herr = 0, any = 1;
   long long iters = 0;
   const int U = 8;   // attempts per graph launch
-  const dim3 ggrid((unsigned)(N / tc::BM), (unsigned)(2 * T / tc::BN));
+  const dim3 ggrid((unsigned)(N / tc::BM), (unsigned)(2 * T / BNT));
   const unsigned ctl_blocks = (unsigned)((T + 255) / 256);
   const unsigned ew_blocks = (unsigned)std::min<size_t>((TN + 255) / 256, 152 * 16);
   if (st == nullptr) {
@@ -371,15 +374,15 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   EN_RC(tc_split(K, NN, kh, kl, st));
   EN_RC(tc_encode_bf16_2d(&mAh, kh, N, N, tc::BM));
   EN_RC(tc_encode_bf16_2d(&mAl, kl, N, N, tc::BM));
-  EN_RC(tc_encode_bf16_2d(&mBh, vh, 2 * T, N, tc::BN));
-  EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, tc::BN));
-  EN_RC(tc_encode_bf16_2d(&mBh1, vh1, 2 * T, N, tc::BN));
-  EN_RC(tc_encode_bf16_2d(&mBl1, vl1, 2 * T, N, tc::BN));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+  EN_RC(tc_encode_bf16_2d(&mBh, vh, 2 * T, N, BNT));
+  EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, BNT));
+  EN_RC(tc_encode_bf16_2d(&mBh1, vh1, 2 * T, N, BNT));
+  EN_RC(tc_encode_bf16_2d(&mBl1, vl1, 2 * T, N, BNT));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_K1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_F1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
   a.N = (int)N;
   a.T = (int)T;
   a.omega = omega;
@@ -417,11 +420,11 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
   a.Vl = (__nv_bfloat16*)vl;
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
   a.phase = E_K1;
-  ens_gemm_kernel<E_K1><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_K1, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
   a.phase = E_F1;
-  ens_gemm_kernel<E_F1><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_F1, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
   EN_CUDA(cudaGetLastError());
   // ---- U attempts per graph: prologue (Y2 -> copy 0), stage 2 (reads copy 0,
@@ -435,18 +438,23 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
     a.phase = E_B2;
     a.Vh = (__nv_bfloat16*)vh1;
     a.Vl = (__nv_bfloat16*)vl1;
-    ens_gemm_kernel<E_B2><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B2, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     a.phase = E_B3;
     a.Vh = (__nv_bfloat16*)vh;
     a.Vl = (__nv_bfloat16*)vl;
-    ens_gemm_kernel<E_B3><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B3, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
     a.phase = E_B4;
-    ens_gemm_kernel<E_B4><<<ggrid, kEnsThreads, tc::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B4, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
     ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
   }
   EN_CUDA(cudaStreamEndCapture(st, &graph));
   EN_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  if (loop_ms) {
+    EN_CUDA(cudaEventCreate(&ev0));
+    EN_CUDA(cudaEventCreate(&ev1));
+    EN_CUDA(cudaEventRecord(ev0, st));
+  }
   while (any) {
     EN_CUDA(cudaGraphLaunch(exec, st));
     EN_CUDA(cudaMemcpyAsync(&any, a.tr.any_live, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -455,6 +463,12 @@ extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const do
     iters += U;
     if (herr) { rc = BS3_ERR_DEVICE_WAIT; break; }
     if (iters > a.max_attempts + U) break;
+    if (max_lockstep > 0 && iters >= max_lockstep && any) { rc = BS3_ERR_MAX_STEPS; break; }
+  }
+  if (loop_ms) {
+    EN_CUDA(cudaEventRecord(ev1, st));
+    EN_CUDA(cudaEventSynchronize(ev1));
+    EN_CUDA(cudaEventElapsedTime(loop_ms, ev0, ev1));
   }
   ens_gather<<<ew_blocks, 256, 0, st>>>(a, theta_out);
   EN_CUDA(cudaGetLastError());
@@ -469,8 +483,72 @@ done:
     cudaStreamDestroy(own);
   }
   if (exec) cudaGraphExecDestroy(exec);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   if (graph) cudaGraphDestroy(graph);
   cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
   cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
   return rc;
+}
+
+extern "C" int bs3_ensemble_solve_tiled(const float* K, int64_t N, int64_t T, const double* omega,
+                                        const double* theta0, double t0, double t1, double rtol, double atol,
+                                        int tile_n, int64_t max_lockstep, double* theta_out, int64_t* n_acc,
+                                        int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream) {
+  if (tile_n == 0) {
+    // more, narrower tiles when the wide ones would leave SMs idle
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+      return BS3_ERR_CUDA;
+    const int64_t wide = (N / tc::BM) * ((2 * T) / 256);
+    tile_n = ((2 * T) % 256 != 0 || 4 * wide < 3 * (int64_t)sms) ? 128 : 256;
+  }
+  if (tile_n == 256)
+    return ensemble_solve_impl<256>(K, N, T, omega, theta0, t0, t1, rtol, atol, max_lockstep, theta_out, n_acc,
+                                    n_rej, status, lockstep_attempts, stream);
+  if (tile_n == 128)
+    return ensemble_solve_impl<128>(K, N, T, omega, theta0, t0, t1, rtol, atol, max_lockstep, theta_out, n_acc,
+                                    n_rej, status, lockstep_attempts, stream);
+  return BS3_ERR_INVALID_ARG;
+}
+
+extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                                  double t0, double t1, double rtol, double atol, double* theta_out,
+                                  int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
+                                  void* stream) {
+  return bs3_ensemble_solve_tiled(K, N, T, omega, theta0, t0, t1, rtol, atol, 0, 0, theta_out, n_acc, n_rej, status,
+                                  lockstep_attempts, stream);
+}
+
+extern "C" int bs3_ensemble_autotune(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
+                                     double t0, double t1, double rtol, double atol, int64_t lockstep_attempts,
+                                     double* scratch_theta, int* tile_out, double* us_out) {
+  if (!K || !omega || !theta0 || !scratch_theta || !tile_out || lockstep_attempts < 8) return BS3_ERR_INVALID_ARG;
+  int best = 0;
+  double best_us = 0.0;
+  for (const int tile : {256, 128}) {
+    if ((2 * T) % tile != 0 || T < tile / 2) continue;
+    double us = 0.0;
+    // two bounded solves: the first warms up, the second's attempt loop is timed
+    for (int rep = 0; rep < 2; ++rep) {
+      int64_t steps = 0;
+      float ms = 0.f;
+      const int r = tile == 256
+                        ? ensemble_solve_impl<256>(K, N, T, omega, theta0, t0, t1, rtol, atol, lockstep_attempts,
+                                                   scratch_theta, nullptr, nullptr, nullptr, &steps, nullptr, &ms)
+                        : ensemble_solve_impl<128>(K, N, T, omega, theta0, t0, t1, rtol, atol, lockstep_attempts,
+                                                   scratch_theta, nullptr, nullptr, nullptr, &steps, nullptr, &ms);
+      if (r != BS3_OK && r != BS3_ERR_MAX_STEPS) return r;
+      us = 1e3 * ms / (double)std::max<int64_t>(1, steps);
+    }
+    if (best == 0 || us < best_us) {
+      best = tile;
+      best_us = us;
+    }
+  }
+  if (best == 0) return BS3_ERR_INVALID_ARG;
+  *tile_out = best;
+  if (us_out) *us_out = best_us;
+  return BS3_OK;
 }

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                    const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, float* C,
                    long long ldc, int K, int* err, long long spin) {
   const tc::StoreRowMajor st{C, ldc};
-  tc::gemm_tile<4>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, st, err, spin);
+  tc::gemm_tile<4, tc::BN>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, st, err, spin);
 }
 
 namespace {

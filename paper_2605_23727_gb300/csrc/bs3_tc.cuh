@@ -18,14 +18,31 @@
 namespace bs3 {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2;
+constexpr int BM = 128, BK = 64, STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;                  // 16 KB per bf16 operand tile
-constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+// Tile of BM x BNT outputs (BNT = 256 or 128 accumulator columns in TMEM).
+template <int BNT>
+struct Tile {
+  static_assert(BNT == 128 || BNT == 256, "tile width");
+  static constexpr int BN = BNT;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = BN;
+  // instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+  // K-major, N = BN, M = BM
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+};
+
+// the plain product's tile
+constexpr int BN = 256;
+constexpr int B_BYTES = Tile<BN>::B_BYTES;
+constexpr int STAGE_BYTES = Tile<BN>::STAGE_BYTES;
+constexpr int SMEM_BYTES = Tile<BN>::SMEM_BYTES;
 constexpr int THREADS = 192;                      // plain product: four epilogue warps
 constexpr int threads_for(int ew) { return 64 + 32 * ew; }
-constexpr int TMEM_COLS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -66,16 +83,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
-// K-major, N = BN, M = BM.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -113,13 +126,15 @@ struct StoreRowMajor {
   }
 };
 
-template <int EW, class Store>
+template <int EW, int BNT, class Store>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensorMap* mAl, const CUtensorMap* mBh,
                                           const CUtensorMap* mBl, int m0, int n0, int K, const Store& store,
                                           int* err, long long spin) {
+  using TL = Tile<BNT>;
+  constexpr int BNL = TL::BN, B_BYTESL = TL::B_BYTES, STAGE_BYTESL = TL::STAGE_BYTES, TMEM_COLSL = TL::TMEM_COLS;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTESL);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -138,7 +153,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(TMEM_COLSL)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -158,12 +173,12 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
         break;
       }
       if (*(volatile int*)s_abort) break;
-      unsigned char* st = base + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
+      unsigned char* st = base + s * STAGE_BYTESL;
+      mbar_expect_tx(&full[s], STAGE_BYTESL);
       tma_load_2d(st, mAh, &full[s], kb * BK, m0);
       tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BK, m0);
       tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BK, n0);
-      tma_load_2d(st + 2 * A_BYTES + B_BYTES, mBl, &full[s], kb * BK, n0);
+      tma_load_2d(st + 2 * A_BYTES + B_BYTESL, mBl, &full[s], kb * BK, n0);
       issued = kb + 1;
     }
     // the copies of the last stages must land before the CTA ends
@@ -179,17 +194,17 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
         break;
       }
       fence_after();
-      const unsigned char* st = base + s * STAGE_BYTES;
+      const unsigned char* st = base + s * STAGE_BYTESL;
       const uint64_t dAh = sw128_desc(smem_u32(st));
       const uint64_t dAl = sw128_desc(smem_u32(st + A_BYTES));
       const uint64_t dBh = sw128_desc(smem_u32(st + 2 * A_BYTES));
-      const uint64_t dBl = sw128_desc(smem_u32(st + 2 * A_BYTES + B_BYTES));
+      const uint64_t dBl = sw128_desc(smem_u32(st + 2 * A_BYTES + B_BYTESL));
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes further along K
-        mma_bf16(tmem, dAh + o, dBh + o, (kb | kk) != 0);
-        mma_bf16(tmem, dAh + o, dBl + o, 1);
-        mma_bf16(tmem, dAl + o, dBh + o, 1);
+        mma_bf16(tmem, dAh + o, dBh + o, TL::IDESC, (kb | kk) != 0);
+        mma_bf16(tmem, dAh + o, dBl + o, TL::IDESC, 1);
+        mma_bf16(tmem, dAl + o, dBh + o, TL::IDESC, 1);
       }
       mma_commit(&empty[s]);
     }
@@ -205,7 +220,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
       const int sub = (warp - 2) >> 2;   // which of the EW/4 warps of this quarter
       const int row = m0 + quarter * 32 + lane;
 #pragma unroll 1
-      for (int c = sub; c < BN / 32; c += EW / 4) {
+      for (int c = sub; c < BNL / 32; c += EW / 4) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), v);
         store(row, n0 + c * 32, v);
@@ -216,7 +231,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
   __syncthreads();
   if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLSL) : "memory");
   }
 }
 

@@ -66,3 +66,51 @@ def test_ensemble_trajectories_are_independent():
         outs.append((out.cpu().numpy()[0], n_acc[0], n_rej[0]))
     assert outs[0][1:] == outs[1][1:]
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
+
+
+def test_tile_widths_agree():
+    """128- and 256-column output tiles give the same trajectories (each output
+    is the same sum over K in the same order) and the same decisions."""
+    bs3 = library()
+    torch = torch_cuda()
+    N, T, t1 = 256, 128, 5.0
+    K, omega, theta0 = W.kuramoto_ensemble(T=T, N=N, seed=6)
+    Kd = torch.tensor(K, dtype=torch.float32, device="cuda")
+    om = torch.tensor(omega, dtype=torch.float64, device="cuda")
+    th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
+    res = {}
+    for tile in (256, 128):
+        out = torch.empty_like(th)
+        rc, n_acc, n_rej, status, _ = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, 1e-6, 1e-6, out, tile_n=tile)
+        assert rc == bs3.OK and np.all(status == 0)
+        res[tile] = (out.cpu().numpy(), n_acc, n_rej)
+    np.testing.assert_array_equal(res[128][1], res[256][1])
+    np.testing.assert_array_equal(res[128][2], res[256][2])
+    np.testing.assert_allclose(res[128][0], res[256][0], rtol=0, atol=1e-9)
+
+
+def test_tile_autotuner_and_narrow_ensembles():
+    bs3 = library()
+    torch = torch_cuda()
+    N, T = 256, 64   # only the 128-column tile fits 2T = 128
+    K, omega, theta0 = W.kuramoto_ensemble(T=T, N=N, seed=7)
+    Kd = torch.tensor(K, dtype=torch.float32, device="cuda")
+    om = torch.tensor(omega, dtype=torch.float64, device="cuda")
+    th = torch.tensor(theta0, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(th)
+    rc, tile, us = bs3.bs3_ensemble_autotune(Kd, N, T, om, th, 0.0, 5.0, 1e-6, 1e-6, 16, out)
+    assert rc == bs3.OK and tile == 128 and us > 0.0
+    assert bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, 5.0, 1e-6, 1e-6, out, tile_n=256)[0] == bs3.ERR_INVALID_ARG
+    rc, n_acc, n_rej, status, _ = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, 5.0, 1e-6, 1e-6, out)
+    assert rc == bs3.OK and np.all(status == 0)
+    # a bounded solve stops early with MAX_STEPS
+    rc, *_ = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, 5.0, 1e-6, 1e-6, out, max_lockstep=8)
+    assert rc == bs3.ERR_MAX_STEPS
+    # the autotuner chooses between both widths when both fit
+    T2 = 128
+    K2, om2, th2 = W.kuramoto_ensemble(T=T2, N=N, seed=8)
+    out2 = torch.empty((T2, N), dtype=torch.float64, device="cuda")
+    rc, tile, _ = bs3.bs3_ensemble_autotune(torch.tensor(K2, dtype=torch.float32, device="cuda"), N, T2,
+                                            torch.tensor(om2, device="cuda"), torch.tensor(th2, device="cuda"),
+                                            0.0, 5.0, 1e-6, 1e-6, 16, out2)
+    assert rc == bs3.OK and tile in (128, 256)
