@@ -126,8 +126,8 @@ __device__ __forceinline__ void put_jv(const Args& a, int buf, int i, const doub
       float s, c;
       if (single) sincosf((float)Y[0], &s, &c);
       else sincos_f_of_d(Y[0], &s, &c);
-      a.jv32[o0] = s;
-      a.jv32[o1] = c;
+      // binary32 j-vector of Kuramoto: interleaved (sin, cos) pairs
+      reinterpret_cast<float2*>(a.jv32 + (size_t)(buf * 2) * a.ld)[i] = make_float2(s, c);
     } else {
       double s, c;
       sincos(Y[0], &s, &c);
@@ -167,6 +167,13 @@ __device__ __forceinline__ void group_bar(int g, int gt) {
   else asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(gt) : "memory");
 }
 
+// A thread's packed partial sums into its accumulator (hi and lo parts of
+// the float-float sum; lo is zero for binary32 sums).
+__device__ __forceinline__ void set_packed(Acc<M_SS>& x, float hi, float) { x.s = hi; }
+__device__ __forceinline__ void set_packed(Acc<M_SD2>& x, float hi, float lo) { x.hi = hi; x.lo = lo; }
+__device__ __forceinline__ void set_packed(Acc<M_SD64>&, float, float) {}
+__device__ __forceinline__ void set_packed(Acc<M_DD>&, float, float) {}
+
 // ---------------------------------------------------------------------------
 // Coupling partial sums of one row block (rows row0 .. row0+nrows-1) for the
 // columns of thread lt of a 128-thread group; then a warp-level reduction.
@@ -184,6 +191,13 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
   const float* v32 = a.jv32 + (size_t)(buf * 2) * a.ld;
   const double* v64 = a.jv64 + (size_t)(buf * 2) * a.ld;
   const unsigned long long pol = l2_policy(a.l2_keep != 0);
+  // Kuramoto with binary32 sums (Sigma = S, or the float-float Sigma = D):
+  // the sine and cosine sums of a row advance together in packed f32x2
+  // instructions, lane by lane the scalar operations (same results)
+  constexpr bool PACKED = (NV == 2) && (MODE == M_SS || MODE == M_SD2);
+  unsigned long long acc2[RB], lo2[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) acc2[r] = lo2[r] = 0ull;
 #pragma unroll(VEC >= 16 ? 1 : 2)
   for (int col = lt * VEC; col < a.ld; col += gt * VEC) {
     uint4 raw[RB];
@@ -193,7 +207,41 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
       raw[r] = (r < nrows) ? (RES ? *reinterpret_cast<const uint4*>(p) : ld_stream16_pol(p, pol))
                            : make_uint4(0u, 0u, 0u, 0u);
     }
-    if (!DD) {
+    if (!DD && NV == 2) {
+      // interleaved (sin, cos) of the columns col .. col + VEC - 1
+      const float4* src = reinterpret_cast<const float4*>(v32 + 2 * (size_t)col);
+      unsigned long long sc[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC / 2; ++q) {
+        const float4 t = src[q];
+        sc[2 * q] = pk2(t.x, t.y);
+        sc[2 * q + 1] = pk2(t.z, t.w);
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+          const float k = L::f(raw[r], e);
+          if (PACKED) {
+            const unsigned long long k2 = pk2(k, k);
+            if (MODE == M_SS) {
+              acc2[r] = fma2(k2, sc[e], acc2[r]);
+            } else {   // two_sum of (hi, k v), then lo += e, for both sums at once
+              const unsigned long long p = mul2(k2, sc[e]);
+              const unsigned long long sm = add2(acc2[r], p);
+              const unsigned long long bb = sub2(sm, acc2[r]);
+              const unsigned long long er = add2(sub2(acc2[r], sub2(sm, bb)), sub2(p, bb));
+              acc2[r] = sm;
+              lo2[r] = add2(lo2[r], er);
+            }
+          } else {
+            float sv0, sv1;
+            upk2(sc[e], sv0, sv1);
+            acc[r][0].add_f(k, sv0);
+            acc[r][NV - 1].add_f(k, sv1);
+          }
+        }
+    } else if (!DD) {
       float vv[NV][VEC];
 #pragma unroll
       for (int n = 0; n < NV; ++n) {
@@ -236,6 +284,16 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
 #pragma unroll
           for (int n = 0; n < NV; ++n) acc[r][n].add_d(k, vv[n][e]);
         }
+    }
+  }
+  if (PACKED) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      float a0, a1, l0, l1;
+      upk2(acc2[r], a0, a1);
+      upk2(lo2[r], l0, l1);
+      set_packed(acc[r][0], a0, l0);
+      set_packed(acc[r][NV - 1], a1, l1);
     }
   }
 #pragma unroll
