@@ -118,7 +118,8 @@ template <int KIND> struct Dim { static constexpr int d = (KIND == K_KURAMOTO) ?
 // stage argument; sin and cos of it for Kuramoto).
 // ---------------------------------------------------------------------------
 template <int KIND>
-__device__ __forceinline__ void put_jv(const Args& a, int buf, int i, const double* Y, int g, bool single) {
+__device__ __forceinline__ void put_jv(const Args& a, int buf, int i, const double* Y, int g, bool single,
+                                       float2* cache = nullptr) {
   const size_t o0 = (size_t)(buf * 2) * a.ld + i;
   const size_t o1 = o0 + a.ld;
   if (KIND == K_KURAMOTO) {
@@ -128,6 +129,7 @@ __device__ __forceinline__ void put_jv(const Args& a, int buf, int i, const doub
       else sincos_f_of_d(Y[0], &s, &c);
       // binary32 j-vector of Kuramoto: interleaved (sin, cos) pairs
       reinterpret_cast<float2*>(a.jv32 + (size_t)(buf * 2) * a.ld)[i] = make_float2(s, c);
+      if (cache) *cache = make_float2(s, c);   // the i-side finish of the next stage reads them
     } else {
       double s, c;
       sincos(Y[0], &s, &c);
@@ -395,14 +397,20 @@ struct RowPar {
 
 template <int KIND>
 __device__ __forceinline__ void finish(const Args& a, const RowPar& rp, const double* Y, double s0, double s1,
-                                       Prec p, bool single, double* K) {
+                                       Prec p, bool single, double* K, const float2* cached = nullptr) {
   if (KIND == K_KURAMOTO) {
     if (p.s == 0) {
       const float sc = rp.scale;
       const float S = (float)s0 * sc, C = (float)s1 * sc;
       float si, ci;
-      if (single) sincosf((float)Y[0], &si, &ci);
-      else sincos_f_of_d(Y[0], &si, &ci);
+      if (cached) {   // the same values, from this row's j-vector of this stage argument
+        si = cached->x;
+        ci = cached->y;
+      } else if (single) {
+        sincosf((float)Y[0], &si, &ci);
+      } else {
+        sincos_f_of_d(Y[0], &si, &ci);
+      }
       const float cpl = ci * S - si * C;
       K[0] = p.f == 0 ? (double)((float)rp.par + cpl) : rp.par + (double)cpl;
     } else {
@@ -500,6 +508,7 @@ struct Ctx {
   double* sth;        // shared k1/(k0-k1)
   double* srs;        // shared row sums
   float* sscale;      // shared row scales
+  float2* sisc;       // shared binary32 (sin, cos) of each row's last j-vector (Kuramoto), or null
   int rc, rb, nr;
   int rank, nb;      // this CTA's place in the group of CTAs that solves the system (nb = 1: alone)
   int iX, iXn, iK1, iK2, iK3, iK4;
@@ -575,7 +584,7 @@ __device__ __forceinline__ void epilogue_dp(const Args& a, Ctx& x, int l, int li
   double Y[d], K[d];
 #pragma unroll
   for (int c = 0; c < d; ++c) Y[c] = (l == 7) ? sv<KIND>(x, x.iXn, c, li) : dp_arg<KIND>(x, l, c, li);
-  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K);
+  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K, x.sisc ? x.sisc + li : nullptr);
 #pragma unroll
   for (int c = 0; c < d; ++c) sv<KIND>(x, dp_slot(x, l), c, li) = K[c];
   if (l < 7) {
@@ -584,7 +593,7 @@ __device__ __forceinline__ void epilogue_dp(const Args& a, Ctx& x, int l, int li
       Y[c] = dp_arg<KIND>(x, l + 1, c, li);
       if (l + 1 == 7) sv<KIND>(x, x.iXn, c, li) = Y[c];
     }
-    put_jv<KIND>(a, (l + 1) & 1, i, Y, x.pn.g, x.single);
+    put_jv<KIND>(a, (l + 1) & 1, i, Y, x.pn.g, x.single, x.sisc ? x.sisc + li : nullptr);
     return;
   }
 #pragma unroll
@@ -642,7 +651,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int l
       default: Y[c] = xo; break;   // PH_RHS, PH_K1
     }
   }
-  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K);
+  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K, x.sisc ? x.sisc + li : nullptr);
   switch (phase) {
     case PH_RHS:
 #pragma unroll
@@ -670,7 +679,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int l
         sv<KIND>(x, x.iK2, c, li) = K[c];
         Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c32, K[c], x.single);
       }
-      put_jv<KIND>(a, 1, i, Y, x.pn.g, x.single);
+      put_jv<KIND>(a, 1, i, Y, x.pn.g, x.single, x.sisc ? x.sisc + li : nullptr);
       break;
     case PH_B3:
 #pragma unroll
@@ -688,7 +697,7 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int l
         sv<KIND>(x, x.iXn, c, li) = xn;
         Y[c] = xn;
       }
-      put_jv<KIND>(a, 2, i, Y, x.pn.g, x.single);
+      put_jv<KIND>(a, 2, i, Y, x.pn.g, x.single, x.sisc ? x.sisc + li : nullptr);
       break;
     default:  // PH_B4: K4 and the error of Eq. ERROR-O23
 #pragma unroll
@@ -800,9 +809,10 @@ __device__ __forceinline__ double ld_bits(const unsigned long long* p) {
 
 // Shared-memory bytes of a launch: the state slots [slots][d][rc] (six for
 // Bogacki-Shampine, nine for Dormand-Prince) plus per-agent
-// parameters (three binary64 and one binary32 per agent).
+// parameters (three binary64 and one binary32 per agent) and a binary32
+// (sin, cos) pair per agent.
 __host__ __device__ constexpr size_t state_smem_bytes(int d, int rc, int slots = 6) {
-  return (size_t)rc * (slots * d * 8 + 3 * 8 + 4) + 16;
+  return (size_t)rc * (slots * d * 8 + 3 * 8 + 4 + 8) + 16;
 }
 
 
@@ -861,7 +871,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       double Y[d];
 #pragma unroll
       for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
-      put_jv<KIND>(a, 0, x.rb + li, Y, x.p.g, single);
+      put_jv<KIND>(a, 0, x.rb + li, Y, x.p.g, single, x.sisc ? x.sisc + li : nullptr);
     }
     if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) return;
     stage<KIND, ST>(a, x, PH_RHS, 0, s_grp);
@@ -889,7 +899,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       double Y[d];
 #pragma unroll
       for (int c = 0; c < d; ++c) Y[c] = sv<KIND>(x, x.iX, c, li);
-      put_jv<KIND>(a, 0, x.rb + li, Y, plast.g, single);
+      put_jv<KIND>(a, 0, x.rb + li, Y, plast.g, single, x.sisc ? x.sisc + li : nullptr);
     }
   }
   if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
@@ -920,7 +930,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
 #pragma unroll
         for (int c = 0; c < d; ++c)
           Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.h0s, sv<KIND>(x, x.iK1, c, li), single);
-        put_jv<KIND>(a, 1, x.rb + li, Y, plast.g, single);
+        put_jv<KIND>(a, 1, x.rb + li, Y, plast.g, single, x.sisc ? x.sisc + li : nullptr);
       }
       if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) goto finish_up;
       x.m0 = 0.0;
@@ -983,7 +993,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         double Y[d];
 #pragma unroll
         for (int c = 0; c < d; ++c) Y[c] = dp_arg<KIND>(x, 2, c, li);
-        put_jv<KIND>(a, 0, x.rb + li, Y, variant_prec_dp(a.variant, 2).g, single);
+        put_jv<KIND>(a, 0, x.rb + li, Y, variant_prec_dp(a.variant, 2).g, single, x.sisc ? x.sisc + li : nullptr);
       }
       if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
       if (rec) ts[1] = globaltimer_ns();
@@ -1010,7 +1020,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
 #pragma unroll
           for (int c = 0; c < d; ++c)
             Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
-          put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single);
+          put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single, x.sisc ? x.sisc + li : nullptr);
         }
         if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
         if (rec) ts[1] = globaltimer_ns();
@@ -1201,6 +1211,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   x.sth = x.spar + x.rc;
   x.srs = x.sth + x.rc;
   x.sscale = (float*)(x.srs + x.rc);
+  x.sisc = (float2*)(((uintptr_t)(x.sscale + x.rc) + 7) & ~(uintptr_t)7);
   x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
   x.iK7 = 8;   // Dormand-Prince: K_l in slot l + 1 (nine slots)
   x.rtol = a.rtol;
@@ -1334,6 +1345,7 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   x.srs = const_cast<double*>(D.rowsum) + x.rb;
   x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum) + x.rb;   // read only by the circadian kind
   x.sscale = const_cast<float*>(D.scale) + x.rb;
+  x.sisc = nullptr;
   x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
   x.rtol = a.rtol;
   x.thr = a.atol / a.rtol;
