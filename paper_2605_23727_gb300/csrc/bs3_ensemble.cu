@@ -57,6 +57,7 @@ struct EArgs {
   __nv_bfloat16* Vh;     // [2T][N] j-vector operand the epilogue writes (the copy not being read)
   __nv_bfloat16* Vl;     // [2T][N]
   float2* SC;            // [T][N] binary32 (sin, cos) of the current stage argument
+  float2* SCX;           // [2][T][N] binary32 (sin, cos) of the states X (selected like X)
   Traj tr;
   double rtol, atol, t1, hmax, hmin;
   long long max_attempts, max_rejects;
@@ -65,9 +66,8 @@ struct EArgs {
 constexpr double kB1 = 2.0 / 9.0, kB2 = 1.0 / 3.0, kB3 = 4.0 / 9.0;
 constexpr double kE1 = -5.0 / 72.0, kE2 = 1.0 / 12.0, kE3 = 1.0 / 9.0, kE4 = -1.0 / 8.0;
 
-__device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
-  float s, c;
-  sincos_f_of_d(y, &s, &c);
+// j-vector entry (bf16 hi/lo of sin and cos) and the binary32 pair of a stage argument
+__device__ __forceinline__ void put_sc(const EArgs& a, int b, int i, float s, float c) {
   a.SC[(size_t)b * a.N + i] = make_float2(s, c);
   const __nv_bfloat16 sh = __float2bfloat16_rn(s), ch = __float2bfloat16_rn(c);
   const size_t rs = (size_t)(2 * b) * a.N + i, rc = rs + a.N;
@@ -75,6 +75,24 @@ __device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
   a.Vl[rs] = __float2bfloat16_rn(s - __bfloat162float(sh));
   a.Vh[rc] = ch;
   a.Vl[rc] = __float2bfloat16_rn(c - __bfloat162float(ch));
+}
+
+__device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
+  float s, c;
+  sincos_f_of_d(y, &s, &c);
+  put_sc(a, b, i, s, c);
+}
+
+// Stage argument X + delta with small delta (h/2 K1, 3h/4 K2): sin and cos by
+// angle addition from those of X, in binary32 (within ~2 ulp of the binary32
+// rounding; binary64 is scarce on GB300 and the full reduction of a new phase
+// costs five binary64 operations, this two).
+__device__ __forceinline__ void put_v_shift(const EArgs& a, int b, int i, float2 scx, double delta) {
+  float sd, cd;
+  sincosf((float)delta, &sd, &cd);
+  const float s = fmaf(scx.x, cd, scx.y * sd);
+  const float c = fmaf(scx.y, cd, -(scx.x * sd));
+  put_sc(a, b, i, s, c);
 }
 
 // Integer tests on the exponent field (binary64 compares issue at the binary64
@@ -124,7 +142,7 @@ struct Epilogue {
     for (int j0 = 0; j0 < 16; j0 += G) {
       int live[G], xs[G], ks[G];
       double x[G], om[G], k1[G], k2[G], k3[G], y[G];
-      float2 sc[G];
+      float2 sc[G], scx[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int b = col0 / 2 + j0 + g;
@@ -134,7 +152,10 @@ struct Epilogue {
         ks[g] = a.tr.ksel[b];
         sc[g] = a.SC[o];   // sin, cos of this stage's argument (agent i)
         om[g] = a.omega[o];
-        x[g] = a.X[xs[g] * slot + o];
+        // stage 2 needs only the sin/cos of X (its next argument X + 3h/4 K2 by
+        // angle addition); the others need X itself
+        x[g] = (PH != E_B2) ? a.X[xs[g] * slot + o] : 0.0;
+        scx[g] = (PH == E_B2) ? a.SCX[xs[g] * slot + o] : make_float2(0.f, 0.f);
         k1[g] = (PH == E_F1 || PH == E_B3 || PH == E_B4) ? a.K14[ks[g] * slot + o] : 0.0;
         k2[g] = (PH == E_B3 || PH == E_B4) ? a.K2[o] : 0.0;
         k3[g] = (PH == E_B4) ? a.K3[o] : 0.0;
@@ -162,12 +183,15 @@ struct Epilogue {
           if (lane == 0) atomicMax(&a.tr.red2[b], (unsigned long long)__double_as_longlong(m));
         } else if (PH == E_B2) {
           a.K2[o] = k;
-          put_v(a, b, i, fma(a.tr.c32[b], k, x[g]));
+          put_v_shift(a, b, i, scx[g], a.tr.c32[b] * k);
         } else if (PH == E_B3) {
           a.K3[o] = k;
           const double xn = fma(a.tr.hs[b], fma(kB3, k, fma(kB2, k2[g], kB1 * k1[g])), x[g]);
           a.X[(1 - xs[g]) * slot + o] = xn;
-          put_v(a, b, i, xn);
+          float sn, cn;
+          sincos_f_of_d(xn, &sn, &cn);
+          put_sc(a, b, i, sn, cn);
+          a.SCX[(1 - xs[g]) * slot + o] = make_float2(sn, cn);   // X' (the state after acceptance)
         } else {
           a.K14[(1 - ks[g]) * slot + o] = k;
           const double dv = a.tr.hs[b] * fma(kE4, k, fma(kE3, k3[g], fma(kE2, k2[g], kE1 * k1[g])));
@@ -201,10 +225,20 @@ __global__ void ens_prologue(EArgs a, int which) {
     const int b = (int)(e / a.N), i = (int)(e % a.N);
     if (!a.tr.live[b]) continue;
     const size_t slot = (size_t)a.T * a.N;
-    const double x = a.X[a.tr.xsel[b] * slot + e];
-    const double k1 = a.K14[a.tr.ksel[b] * slot + e];
-    const double c = which == 0 ? 0.0 : (which == 1 ? a.tr.h0[b] : a.tr.c21[b]);
-    put_v(a, b, i, which == 0 ? x : fma(c, k1, x));
+    const int xs = a.tr.xsel[b];
+    if (which == 2) {   // Y2 = X + h/2 K1 by angle addition from the sin/cos of X
+      put_v_shift(a, b, i, a.SCX[xs * slot + e], a.tr.c21[b] * a.K14[a.tr.ksel[b] * slot + e]);
+      continue;
+    }
+    const double x = a.X[xs * slot + e];
+    if (which == 0) {
+      float s0, c0;
+      sincos_f_of_d(x, &s0, &c0);
+      put_sc(a, b, i, s0, c0);
+      a.SCX[xs * slot + e] = make_float2(s0, c0);   // the initial state's pair
+    } else {
+      put_v(a, b, i, fma(a.tr.h0[b], a.K14[a.tr.ksel[b] * slot + e], x));
+    }
   }
 }
 
@@ -323,7 +357,8 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   cudaStream_t own = nullptr;   // graphs cannot be captured on the legacy default stream
   int rc = BS3_OK;
   const size_t NN = (size_t)N * N, TN = (size_t)T * N;
-  void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr, *vh1 = nullptr, *vl1 = nullptr, *scb = nullptr;
+  void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr, *vh1 = nullptr, *vl1 = nullptr, *scb = nullptr,
+       *scx = nullptr;
   double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *K3 = nullptr, *dsc = nullptr;
   int *isc = nullptr, *derr = nullptr;
   long long* lsc = nullptr;
@@ -352,6 +387,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaMalloc(&vh1, 2 * TN * 2));
   EN_CUDA(cudaMalloc(&vl1, 2 * TN * 2));
   EN_CUDA(cudaMalloc(&scb, TN * sizeof(float2)));
+  EN_CUDA(cudaMalloc(&scx, 2 * TN * sizeof(float2)));
   EN_CUDA(cudaMalloc(&X, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K14, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K2, TN * sizeof(double)));
@@ -366,6 +402,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaMemsetAsync(vh1, 0, 2 * TN * 2, st));
   EN_CUDA(cudaMemsetAsync(vl1, 0, 2 * TN * 2, st));
   EN_CUDA(cudaMemsetAsync(scb, 0, TN * sizeof(float2), st));
+  EN_CUDA(cudaMemsetAsync(scx, 0, 2 * TN * sizeof(float2), st));
   EN_CUDA(cudaMemsetAsync(isc, 0, (6 * T + 1) * sizeof(int), st));
   EN_CUDA(cudaMemsetAsync(lsc, 0, 3 * T * sizeof(long long), st));
   EN_CUDA(cudaMemsetAsync(usc, 0, 4 * T * sizeof(unsigned long long), st));
@@ -393,6 +430,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   a.Vh = (__nv_bfloat16*)vh;
   a.Vl = (__nv_bfloat16*)vl;
   a.SC = (float2*)scb;
+  a.SCX = (float2*)scx;
   a.tr.t = dsc; a.tr.h = dsc + T; a.tr.h0 = dsc + 2 * T; a.tr.c21 = dsc + 3 * T; a.tr.c32 = dsc + 4 * T;
   a.tr.hs = dsc + 5 * T;
   a.tr.live = isc; a.tr.xsel = isc + T; a.tr.ksel = isc + 2 * T; a.tr.last = isc + 3 * T; a.tr.rej = isc + 4 * T;
@@ -486,7 +524,7 @@ done:
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (graph) cudaGraphDestroy(graph);
-  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
+  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(scx); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
   cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
   return rc;
 }
