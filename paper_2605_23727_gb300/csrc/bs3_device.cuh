@@ -88,32 +88,28 @@ __device__ __forceinline__ uint4 ld_stream16_pol(const void* p, unsigned long lo
   return r;
 }
 
-// q^(1/3) for the step-size controller, q > 0.  A dependent binary64 op
-// costs ~30 ns on GB300 and pow() ~3 us, all on the serial path of every
-// attempt; instead: the binary32 cube root (relative error ~1e-7), then one
-// Newton step y - (y^3 - q) / (3 y^2) in binary64 with a binary32 estimate of
-// 1 / (3 y^2), which leaves a relative error of ~1e-14.  q is clamped to
-// [1e-30, 1e30]; beyond [0.24, 245] the controller's limits (factor in
-// [0.5, 5] with safety factor 0.8) decide the step anyway.
-__device__ __forceinline__ double cbrt_pos(double q) {
-  q = fmin(fmax(q, 1e-30), 1e30);
-  const float yf = cbrtf((float)q);
+// (n / d)^(1/3) and (n / d)^(1/5) for n, d > 0 without a binary64 division
+// (~210 ns of latency on GB300): a binary32 seed of the root of the binary32
+// quotient, then one Newton step on y^k d = n in binary64 with a binary32
+// estimate of 1 / (k y^(k-1) d); relative error ~1e-14.  The seed's quotient
+// is clamped to [1e-30, 1e30]; at the clamps (and when d under- or
+// overflows binary32) the step returns +Inf or the clamped root, beyond the
+// controller's limits either way.
+__device__ __forceinline__ double cbrt_ratio(double n, double d) {
+  const float df = (float)d;
+  const float yf = cbrtf(fminf(fmaxf(__fdividef((float)n, df), 1e-30f), 1e30f));
   const double y = (double)yf;
-  const double r = (double)(1.0f / (3.0f * yf * yf));
-  return fma(-fma(y * y, y, -q), r, y);
+  const double r = (double)(1.0f / (3.0f * yf * yf * df));
+  return fma(-fma((y * y) * y, d, -n), r, y);
 }
 
-// q^(1/5) for the controller of the fifth-order pair, q > 0: a binary32 seed
-// (log2/exp2) refined by one Newton step y - (y^5 - q) / (5 y^4) in binary64
-// with a binary32 estimate of 1 / (5 y^4) (relative error ~1e-14).  Clamped
-// like cbrt_pos; outside [0.095, 9537] the controller's limits decide.
-__device__ __forceinline__ double root5_pos(double q) {
-  q = fmin(fmax(q, 1e-30), 1e30);
-  const float yf = exp2f(0.2f * log2f((float)q));
+__device__ __forceinline__ double root5_ratio(double n, double d) {
+  const float df = (float)d;
+  const float yf = exp2f(0.2f * log2f(fminf(fmaxf(__fdividef((float)n, df), 1e-30f), 1e30f)));
   const double y = (double)yf;
   const double y2 = y * y, y4 = y2 * y2;
-  const double r = (double)(1.0f / (5.0f * (float)y4));
-  return fma(-fma(y4, y, -q), r, y);
+  const double r = (double)(1.0f / (5.0f * (yf * yf) * (yf * yf) * df));
+  return fma(-fma(y4 * y, d, -n), r, y);
 }
 
 // Grid barrier for a cooperative launch.  Every CTA adds one arrival to a

@@ -300,13 +300,13 @@ __global__ void ens_control(EArgs a, int stage) {
             r.xsel[b] ^= 1;
             r.ksel[b] ^= 1;
             ++r.n_acc[b];
-            double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * cbrt_pos(a.rtol / E));
+            double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * cbrt_ratio(a.rtol, E));
             if (r.rej[b]) fac = fmin(1.0, fac);
             r.h[b] = h * fac;
             r.rej[b] = 0;
           } else {
             ++r.n_rej[b];
-            r.h[b] = r.rej[b] ? h * 0.5 : h * fmax(0.5, 0.8 * cbrt_pos(a.rtol / E));
+            r.h[b] = r.rej[b] ? h * 0.5 : h * fmax(0.5, 0.8 * cbrt_ratio(a.rtol, E));
             r.rej[b] = 1;
           }
           next_attempt(a, b);

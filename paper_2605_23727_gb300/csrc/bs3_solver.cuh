@@ -825,6 +825,7 @@ struct Scal {
   long long n_acc, n_rej, n_rhs, next_out, out_end;
   int status, last, stop, accepted, rejected, parity;
   int mlp_go, n_ehist;
+  int cancel;               // the host's cancel flag as the last attempt saw it
   double ehist[4];          // errors of the last accepted steps (learned proposer)
   float feat[kMlpIn];
   double theta[kThetaMax];
@@ -889,7 +890,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
     sc.t = a.t0; sc.h = a.h_given; sc.E = 0.0;
     sc.n_acc = 0; sc.n_rej = 0; sc.n_rhs = 0; sc.next_out = 0; sc.out_end = 0;
     sc.status = S_OK; sc.last = 0; sc.stop = 0; sc.accepted = 0; sc.rejected = 0; sc.parity = 0;
-    sc.mlp_go = 0; sc.n_ehist = 0;
+    sc.mlp_go = 0; sc.n_ehist = 0; sc.cancel = 0;
     if (a.job == JOB_SOLVE)
       while (sc.next_out < a.n_out && a.t_out[sc.next_out] <= a.t0) ++sc.next_out;
   }
@@ -960,7 +961,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         if (!(sc.t < a.t1)) sc.stop = 1;
         else if (sc.n_rej > a.max_rejects) { sc.status = S_MAX_REJECTS; sc.stop = 1; }
         else if (na >= a.max_attempts) { sc.status = S_MAX_STEPS; sc.stop = 1; }
-        else if (na > 0 && __ldcg(&ctrl->cancel_seen[sc.parity ^ 1])) { sc.status = S_TIMEOUT; sc.stop = 1; }
+        else if (na > 0 && sc.cancel) { sc.status = S_TIMEOUT; sc.stop = 1; }
         else {
           double h = fmin(sc.h, a.hmax);
           if (h <= a.hmin) { sc.status = S_STEP_TOO_SMALL; sc.stop = 1; }
@@ -1051,6 +1052,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
     // ---- decision (thread 0; warp 0 runs the learned proposer when installed)
     if (tid == 0) {
       const double E = ld_bits(&ctrl->emax[parity]);
+      sc.cancel = __ldcg(&ctrl->cancel_seen[parity]);   // loaded beside E, off the path of the next attempt
       sc.E = E;
       sc.n_rhs += dp ? 6 : 3;
       if (rec) {
@@ -1076,7 +1078,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
           ++e;
         }
         sc.out_end = e;
-        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * (dp ? root5_pos(rtol / E) : cbrt_pos(rtol / E)));
+        double fac = (E == 0.0) ? 5.0 : fmin(5.0, 0.8 * (dp ? root5_ratio(rtol, E) : cbrt_ratio(rtol, E)));
         if (sc.rejected) fac = fmin(1.0, fac);
         sc.h = h * fac;
         sc.t = t_new;
@@ -1098,7 +1100,7 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
         sc.accepted = 1;
       } else {
         ++sc.n_rej;
-        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * (dp ? root5_pos(rtol / E) : cbrt_pos(rtol / E)));
+        sc.h = sc.rejected ? sc.h * 0.5 : sc.h * fmax(0.5, 0.8 * (dp ? root5_ratio(rtol, E) : cbrt_ratio(rtol, E)));
         sc.rejected = 1;
         sc.mlp_go = 0;
       }
