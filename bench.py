@@ -134,8 +134,9 @@ def run_ragged_case(name):
     y0 = np.concatenate([w.y0 for w in systems])
     t0 = np.zeros(count)
     t1 = np.full(count, 10.0)
-    rc, yf, stats, kms = bs3.bs3_batch_solve(bs3.LCO_CFG, Ns, params, K, bs3.F16, y0, t0, t1, RTOL, RTOL,
-                                             bs3.MIXED1, bs3.ACC_FLOAT2)
+    for _ in range(2):     # the first launch pays the one-time set-up
+        rc, yf, stats, kms = bs3.bs3_batch_solve(bs3.LCO_CFG, Ns, params, K, bs3.F16, y0, t0, t1, RTOL, RTOL,
+                                                 bs3.MIXED1, bs3.ACC_FLOAT2)
     evals = np.array([st.n_rhs_evals for st in stats], dtype=np.float64)
     nn = np.array(Ns, dtype=np.float64)
     weight_bytes = float(np.sum(evals * nn * nn * 2))
@@ -435,14 +436,17 @@ def run_case(name):
     sysm = bs3.System.from_workload(w, store)
     y0 = torch.tensor(w.y0, dtype=torch.float64, device="cuda")
     y = torch.empty_like(y0)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    rc, st = bs3.bs3_solve(sysm.handle, w.t0, w.t1, y0, w.rtol, w.atol, bs3.VARIANT_IDS[variant],
-                           bs3.ACC_FLOAT2, None, 0, None, y, 0)
-    e1.record()
-    e1.synchronize()
+    # the first solve pays the one-time set-up (module load, launch plan,
+    # buffers) between its events; the second is timed
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, st = bs3.bs3_solve(sysm.handle, w.t0, w.t1, y0, w.rtol, w.atol, bs3.VARIANT_IDS[variant],
+                               bs3.ACC_FLOAT2, None, 0, None, y, 0)
+        e1.record()
+        e1.synchronize()
     sysm.close()
     ms = e0.elapsed_time(e1)
     out = {"case": name, "status": bs3.bs3_status_string(rc), "ms": ms,

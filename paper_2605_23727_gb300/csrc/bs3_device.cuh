@@ -31,6 +31,7 @@ constexpr int kBlock = 512;          // threads per CTA of the persistent solver
 constexpr int kGroupThreads = 128;   // a warp group: four warps share one row block
 constexpr int kGroups = kBlock / kGroupThreads;
 constexpr int kRBMax = 4;            // largest number of rows per row block
+constexpr int kGrpSlots = (kBlock / 32) * kRBMax * 2;  // one set of per-warp partial sums of a row block
 
 // Rows per row block: the streaming products share each j-vector chunk over 4
 // rows; the pairwise arctangent kernel is ALU-bound and keeps 2.

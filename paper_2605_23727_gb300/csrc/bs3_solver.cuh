@@ -736,6 +736,11 @@ __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int bu
   const int g = threadIdx.x / gt, lt = threadIdx.x % gt;
   const int wig = lt >> 5, lane = lt & 31;
   const int nrb = (x.nr + RB - 1) / RB;
+  // two sets of partial-sum slots, used alternately: a group's warps write the
+  // next row block's sums while its first threads still read this one's, so
+  // one group barrier per row block suffices (the CTA-wide barrier that ends
+  // every stage separates the last reads from the next stage's writes)
+  unsigned long long* slots = red;
   for (int rbk = g; rbk < nrb; rbk += ng) {
     const int lrow0 = rbk * RB;
     const int nrows = min(RB, x.nr - lrow0);
@@ -747,7 +752,7 @@ __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int bu
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int n = 0; n < NV; ++n) red[((wbase + wig) * kRBMax + r) * 2 + n] = pack(acc[r][n]);
+        for (int n = 0; n < NV; ++n) slots[((wbase + wig) * kRBMax + r) * 2 + n] = pack(acc[r][n]);
     }
     group_bar(g, gt);
     if (lt < nrows) {
@@ -755,12 +760,12 @@ __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int bu
 #pragma unroll
       for (int n = 0; n < NV; ++n) {
         Acc<MODE> tot;
-        for (int w = 0; w < wpg; ++w) merge(tot, red[((wbase + w) * kRBMax + lt) * 2 + n]);
+        for (int w = 0; w < wpg; ++w) merge(tot, slots[((wbase + w) * kRBMax + lt) * 2 + n]);
         s[n] = tot.value();
       }
       epilogue<KIND>(a, x, phase, lrow0 + lt, s[0], s[1]);
     }
-    group_bar(g, gt);
+    slots = (slots == red) ? red + kGrpSlots : red;
   }
 }
 
@@ -1193,7 +1198,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ int s_abort;
   __shared__ unsigned long long s_red[kBlock / 32];
-  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
+  __shared__ unsigned long long s_grp[2 * kGrpSlots];
   __shared__ Scal sc;
   const int N = a.N;
   const int G = gridDim.x, b = blockIdx.x;
@@ -1368,7 +1373,7 @@ template <int KIND, int ST>
 __global__ void __launch_bounds__(kBlock, 1) bs3_batch_kernel(BatchArgs ba) {
   __shared__ int s_abort, s_sys;
   __shared__ unsigned long long s_red[kBlock / 32];
-  __shared__ unsigned long long s_grp[(kBlock / 32) * kRBMax * 2];
+  __shared__ unsigned long long s_grp[2 * kGrpSlots];
   __shared__ Scal sc;
   const int tid = threadIdx.x;
   if (ba.team > 1 && (int)blockIdx.x < ba.n_teams * ba.team) {
