@@ -299,9 +299,11 @@ int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega
 
 /* bs3_ensemble_solve with an explicit output tile width and an optional bound.
  * tile_n: 256 (128 x 256 accumulator tiles, 128 trajectories per tile; needs
- * T % 128 == 0), 128 (128 x 128 tiles, 64 trajectories; T % 64 == 0), or 0:
- * 128 when the 256-wide tiles would fill fewer than 3/4 of the SMs (or T is
- * not a multiple of 128), else 256.  max_lockstep > 0 stops after that many
+ * T % 128 == 0), 128 (128 x 128 tiles, 64 trajectories; T % 64 == 0), or 0
+ * (= 128).  Each stage product runs on at most one CTA per SM, each CTA taking
+ * tiles in turn with two accumulators in tensor memory, so that one tile's
+ * epilogue overlaps the next tile's products; the narrower tiles give every
+ * CTA more tiles to overlap.  max_lockstep > 0 stops after that many
  * lock-step attempts (rounded up to the 8 of one graph launch) and returns
  * BS3_ERR_MAX_STEPS if trajectories are still running; 0 = no bound beyond
  * the per-trajectory limits.  The paper has no counterpart. */

@@ -124,7 +124,7 @@ __device__ __forceinline__ double ratio(double n, double d) {
   return n * (r0 * fma(-d, r0, 2.0));
 }
 
-// The stage epilogue run on the accumulator rows of one 128 x 256 tile, one
+// The stage epilogue run on the accumulator rows of one 128-row tile, one
 // instantiation per phase.  Each thread owns one row i and 16 trajectories
 // per call; the inputs of four trajectories are loaded together (also for
 // retired trajectories, whose buffers stay allocated) so that the loads
@@ -209,13 +209,16 @@ struct Epilogue {
 constexpr int kEpiWarps = 16;
 constexpr int kEnsThreads = tc::threads_for(kEpiWarps);
 
+// One stage product over all (N / 128) x (2T / BNT) tiles; persistent CTAs
+// (at most one per SM) take the tiles in turn, each tile's epilogue
+// overlapping the next tile's products.
 template <int PH, int BNT>
 __global__ void __launch_bounds__(kEnsThreads, 1)
     ens_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                     const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, EArgs a, int K,
                     int* err, long long spin) {
   const Epilogue<PH> epi{a};
-  tc::gemm_tile<kEpiWarps, BNT>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * BNT, K, epi, err, spin);
+  tc::gemm_persistent<kEpiWarps, BNT>(&mAh, &mAl, &mBh, &mBl, K / tc::BM, 2 * a.T / BNT, K, epi, err, spin);
 }
 
 // j-vector operand of the stage argument Y = X + c K1 (c = 0, h0 or h/2).
@@ -349,7 +352,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
                         int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
                         void* stream_, float* loop_ms = nullptr) {
   if (!K || !omega || !theta0 || !theta_out) return BS3_ERR_INVALID_ARG;
-  using TL = tc::Tile<BNT>;
+  using PT = tc::PTile<BNT>;
   if (N < tc::BM || N % tc::BM || N % tc::BK || T < BNT / 2 || (2 * T) % BNT) return BS3_ERR_INVALID_ARG;
   if (N > (1 << 20) || T > (1 << 16)) return BS3_ERR_INVALID_ARG;
   if (!(t1 > t0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
@@ -372,7 +375,12 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   int herr = 0, any = 1;
   long long iters = 0;
   const int U = 8;   // attempts per graph launch
-  const dim3 ggrid((unsigned)(N / tc::BM), (unsigned)(2 * T / BNT));
+  int dev = 0, sms = 0;   // (nothing is allocated yet)
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return BS3_ERR_CUDA;
+  const int64_t n_tiles = (N / tc::BM) * (2 * T / BNT);
+  const dim3 ggrid((unsigned)std::min<int64_t>(n_tiles, sms));
   const unsigned ctl_blocks = (unsigned)((T + 255) / 256);
   const unsigned ew_blocks = (unsigned)std::min<size_t>((TN + 255) / 256, 152 * 16);
   if (st == nullptr) {
@@ -415,11 +423,11 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_RC(tc_encode_bf16_2d(&mBl, vl, 2 * T, N, BNT));
   EN_RC(tc_encode_bf16_2d(&mBh1, vh1, 2 * T, N, BNT));
   EN_RC(tc_encode_bf16_2d(&mBl1, vl1, 2 * T, N, BNT));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_K1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_F1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
-  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TL::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_K1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_F1, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
+  EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
   a.N = (int)N;
   a.T = (int)T;
   a.omega = omega;
@@ -458,11 +466,11 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   a.Vl = (__nv_bfloat16*)vl;
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
   a.phase = E_K1;
-  ens_gemm_kernel<E_K1, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_K1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
   ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
   a.phase = E_F1;
-  ens_gemm_kernel<E_F1, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+  ens_gemm_kernel<E_F1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
   ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
   EN_CUDA(cudaGetLastError());
   // ---- U attempts per graph: prologue (Y2 -> copy 0), stage 2 (reads copy 0,
@@ -476,13 +484,13 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
     a.phase = E_B2;
     a.Vh = (__nv_bfloat16*)vh1;
     a.Vl = (__nv_bfloat16*)vl1;
-    ens_gemm_kernel<E_B2, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B2, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     a.phase = E_B3;
     a.Vh = (__nv_bfloat16*)vh;
     a.Vl = (__nv_bfloat16*)vl;
-    ens_gemm_kernel<E_B3, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B3, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
     a.phase = E_B4;
-    ens_gemm_kernel<E_B4, BNT><<<ggrid, kEnsThreads, TL::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
+    ens_gemm_kernel<E_B4, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
     if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
     ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
   }
@@ -533,15 +541,9 @@ extern "C" int bs3_ensemble_solve_tiled(const float* K, int64_t N, int64_t T, co
                                         const double* theta0, double t0, double t1, double rtol, double atol,
                                         int tile_n, int64_t max_lockstep, double* theta_out, int64_t* n_acc,
                                         int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream) {
-  if (tile_n == 0) {
-    // more, narrower tiles when the wide ones would leave SMs idle
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                   cudaSuccess)
-      return BS3_ERR_CUDA;
-    const int64_t wide = (N / tc::BM) * ((2 * T) / 256);
-    tile_n = ((2 * T) % 256 != 0 || 4 * wide < 3 * (int64_t)sms) ? 128 : 256;
-  }
+  // narrow tiles by default: more tiles per persistent CTA, so more of each
+  // binary64 epilogue overlaps the next tile's products
+  if (tile_n == 0) tile_n = 128;
   if (tile_n == 256)
     return ensemble_solve_impl<256>(K, N, T, omega, theta0, t0, t1, rtol, atol, max_lockstep, theta_out, n_acc,
                                     n_rej, status, lockstep_attempts, stream);

@@ -9,6 +9,8 @@
 //   reads tensor-memory lanes 32*(w%4) .. +31; EW/4 warps share each lane
 //   quarter and split its 32-column chunks).
 // Every wait is bounded; a wait that runs out sets *err and the CTA winds down.
+// gemm_persistent is the same pipeline over several tiles per CTA, with two
+// accumulators in tensor memory (see there).
 #pragma once
 
 #include <cuda.h>
@@ -51,6 +53,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   uint32_t ok;
@@ -225,6 +230,180 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mAh, const CUtensor
         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), v);
         store(row, n0 + c * 32, v);
       }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLSL) : "memory");
+  }
+}
+
+// Persistent form: CTA b computes the tiles b, b + gridDim.x, b + 2 gridDim.x,
+// ... of a tiles_m x tiles_n grid of BM x BNT tiles, numbered row block by row
+// block (the column tiles of one row block are consecutive, so the CTAs that
+// run together share the A rows in L2).  The operand ring runs on across
+// tiles, and tensor memory holds two accumulators: the MMA thread fills one
+// while the epilogue warps drain the other, so the epilogue of a tile overlaps
+// the products of the next.  Barriers: full/empty (operand ring), acc_full
+// (MMA -> epilogue, one commit per tile), acc_empty (epilogue -> MMA, one
+// arrival per epilogue warp), mma_done (the last MMAs, before tensor memory
+// is released).
+template <int BNT>
+struct PTile {
+  static constexpr int S = BNT == 128 ? 3 : 2;   // ring stages
+  static constexpr int SMEM_BYTES = S * Tile<BNT>::STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = 2 * BNT;
+};
+
+template <int EW, int BNT, class Store>
+__device__ __forceinline__ void gemm_persistent(const CUtensorMap* mAh, const CUtensorMap* mAl,
+                                                const CUtensorMap* mBh, const CUtensorMap* mBl, int tiles_m,
+                                                int tiles_n, int K, const Store& store, int* err, long long spin) {
+  using TL = Tile<BNT>;
+  constexpr int S = PTile<BNT>::S;
+  constexpr int BNL = TL::BN, B_BYTESL = TL::B_BYTES, STAGE_BYTESL = TL::STAGE_BYTES;
+  constexpr int TMEM_COLSL = PTile<BNT>::TMEM_COLS;
+  static_assert(EW % 4 == 0 && EW >= 4 && EW <= 32, "epilogue warps: a multiple of four");
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + S * STAGE_BYTESL);
+  uint64_t* empty = full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  int* s_abort = reinterpret_cast<int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = K / BK;
+  const int n_tiles = tiles_m * tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], EW);
+    }
+    mbar_init(mma_done, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLSL)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------- producer
+    int it = 0;   // operand stages issued so far (the ring position)
+    bool stop = false;
+    for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
+      const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BNL;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(&empty[s], (uint32_t)(((it / S) & 1) ^ 1), spin)) {
+          atomicExch(err, 1);
+          *(volatile int*)s_abort = 1;
+          stop = true;
+          break;
+        }
+        if (*(volatile int*)s_abort) {
+          stop = true;
+          break;
+        }
+        unsigned char* st = base + s * STAGE_BYTESL;
+        mbar_expect_tx(&full[s], STAGE_BYTESL);
+        tma_load_2d(st, mAh, &full[s], kb * BK, m0);
+        tma_load_2d(st + A_BYTES, mAl, &full[s], kb * BK, m0);
+        tma_load_2d(st + 2 * A_BYTES, mBh, &full[s], kb * BK, n0);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTESL, mBl, &full[s], kb * BK, n0);
+        ++it;
+      }
+    }
+    // the copies of the last stages must land before the CTA ends
+    for (int k = (it > S ? it - S : 0); k < it; ++k) mbar_wait(&full[k % S], (uint32_t)((k / S) & 1), spin);
+  } else if (warp == 1 && lane == 0) {
+    // --------------------------------------------------------------- MMA
+    int it = 0, j = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      // the epilogue has drained this accumulator (tile j - 2)
+      if (j >= 2 && !mbar_wait(&acc_empty[b], (uint32_t)(((j >> 1) & 1) ^ 1), spin)) {
+        atomicExch(err, 1);
+        *(volatile int*)s_abort = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t d = tmem + (uint32_t)(b * BNL);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = it % S;
+        if (*(volatile int*)s_abort || !mbar_wait(&full[s], (uint32_t)((it / S) & 1), spin)) {
+          atomicExch(err, 1);
+          *(volatile int*)s_abort = 1;
+          stop = true;
+          break;
+        }
+        fence_after();
+        const unsigned char* st = base + s * STAGE_BYTESL;
+        const uint64_t dAh = sw128_desc(smem_u32(st));
+        const uint64_t dAl = sw128_desc(smem_u32(st + A_BYTES));
+        const uint64_t dBh = sw128_desc(smem_u32(st + 2 * A_BYTES));
+        const uint64_t dBl = sw128_desc(smem_u32(st + 2 * A_BYTES + B_BYTESL));
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 bf16 = 32 bytes further along K
+          mma_bf16(d, dAh + o, dBh + o, TL::IDESC, (kb | kk) != 0);
+          mma_bf16(d, dAh + o, dBl + o, TL::IDESC, 1);
+          mma_bf16(d, dAl + o, dBh + o, TL::IDESC, 1);
+        }
+        mma_commit(&empty[s]);
+        ++it;
+      }
+      if (!stop) mma_commit(&acc_full[b]);   // fires when this tile's products are complete
+    }
+    // every MMA issued above has completed before tensor memory is released
+    mma_commit(mma_done);
+    mbar_wait(mma_done, 0, spin);
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const int quarter = warp & 3;        // tensor-memory lanes 32*quarter .. 32*quarter+31
+    const int sub = (warp - 2) >> 2;     // which of the EW/4 warps of this quarter
+    int j = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      bool ok = !*(volatile int*)s_abort && mbar_wait(&acc_full[b], (uint32_t)((j >> 1) & 1), spin);
+      fence_after();
+      // one decision per warp: tcgen05.ld below is a warp-wide instruction
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(err, 1);
+          *(volatile int*)s_abort = 1;
+        }
+        break;
+      }
+      const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BNL;
+      const int row = m0 + quarter * 32 + lane;
+#pragma unroll 1
+      for (int c = sub; c < BNL / 32; c += EW / 4) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BNL + c * 32), v);
+        store(row, n0 + c * 32, v);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
   }
   fence_before();

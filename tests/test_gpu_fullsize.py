@@ -1,9 +1,9 @@
 """Full-size workloads in the launch configurations the benchmarks time, checked
 on outputs the oracle can compute one by one or through properties that hold at
 any size: the 256-trajectory ensemble at N = 8192 (closed form when K = 0, and
-trajectory independence), the N = 32768 binary16 oscillators (sampled rows of
-one evaluation), and the 1000-system ragged batch (sampled systems against
-their own solves)."""
+trajectory independence) and at N = 16384 (several tiles per persistent CTA),
+the N = 32768 binary16 oscillators (sampled rows of one evaluation), and the
+1000-system ragged batch (sampled systems against their own solves)."""
 
 import numpy as np
 import pytest
@@ -53,6 +53,37 @@ def test_ensemble_256x8192_members_are_independent():
         else:
             assert res[1:] == first[1:]
             np.testing.assert_array_equal(res[0], first[0])
+
+
+def test_ensemble_persistent_tiles_agree_across_widths():
+    """T = 256 trajectories at N = 16384: with 128-column tiles every CTA of the
+    persistent product takes three or four tiles (512 tiles on at most 152
+    CTAs, both tensor-memory accumulators reused), with 256-column tiles one or
+    two.  Each output is the same sum in the same order either way, so the
+    trajectories and every decision agree; with K = 0 both reproduce the
+    closed form."""
+    bs3 = library()
+    torch = torch_cuda()
+    T, N, t1 = 256, 16384, 0.5
+    K, omega, theta0 = W.kuramoto_ensemble(T=T, N=N, seed=13)
+    om = torch.tensor(omega, device="cuda")
+    th = torch.tensor(theta0, device="cuda")
+    for coupled in (True, False):
+        Kd = torch.tensor(K, device="cuda") if coupled else torch.zeros((N, N), dtype=torch.float32, device="cuda")
+        res = {}
+        for tile in (128, 256):
+            out = torch.empty_like(th)
+            rc, n_acc, n_rej, status, _ = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, 1e-6, 1e-6, out,
+                                                                 tile_n=tile)
+            assert rc == bs3.OK and np.all(status == 0), (coupled, tile)
+            res[tile] = (out.cpu().numpy(), n_acc, n_rej)
+        del Kd
+        np.testing.assert_array_equal(res[128][1], res[256][1])
+        np.testing.assert_array_equal(res[128][2], res[256][2])
+        np.testing.assert_allclose(res[128][0], res[256][0], rtol=0, atol=1e-9)
+        if not coupled:
+            ex = exact.kuramoto_uncoupled(theta0, omega, t1)
+            assert np.max(np.abs(res[128][0] - ex)) <= 1e-12 * (1.0 + np.max(np.abs(ex)))
 
 
 def test_oscillators_32768_f16_sampled_rows():
