@@ -53,7 +53,7 @@ struct EArgs {
   double* X;             // [2][T][N]
   double* K14;           // [2][T][N]: K1 and K4 slots
   double* K2;            // [T][N]
-  double* K3;            // [T][N]
+  double* E3;            // [T][N]: the error's terms through stage 3, e1 K1 + e2 K2 + e3 K3
   __nv_bfloat16* Vh;     // [2T][N] j-vector operand the epilogue writes (the copy not being read)
   __nv_bfloat16* Vl;     // [2T][N]
   float2* SC;            // [T][N] binary32 (sin, cos) of the current stage argument
@@ -141,7 +141,7 @@ struct Epilogue {
 #pragma unroll
     for (int j0 = 0; j0 < 16; j0 += G) {
       int live[G], xs[G], ks[G];
-      double x[G], om[G], k1[G], k2[G], k3[G], y[G];
+      double x[G], om[G], k1[G], k2[G], e3[G], y[G];
       float2 sc[G], scx[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -156,9 +156,9 @@ struct Epilogue {
         // angle addition); the others need X itself
         x[g] = (PH != E_B2) ? a.X[xs[g] * slot + o] : 0.0;
         scx[g] = (PH == E_B2) ? a.SCX[xs[g] * slot + o] : make_float2(0.f, 0.f);
-        k1[g] = (PH == E_F1 || PH == E_B3 || PH == E_B4) ? a.K14[ks[g] * slot + o] : 0.0;
-        k2[g] = (PH == E_B3 || PH == E_B4) ? a.K2[o] : 0.0;
-        k3[g] = (PH == E_B4) ? a.K3[o] : 0.0;
+        k1[g] = (PH == E_F1 || PH == E_B3) ? a.K14[ks[g] * slot + o] : 0.0;
+        k2[g] = (PH == E_B3) ? a.K2[o] : 0.0;
+        e3[g] = (PH == E_B4) ? a.E3[o] : 0.0;
         y[g] = (PH == E_B4) ? a.X[(1 - xs[g]) * slot + o] : 0.0;
       }
 #pragma unroll
@@ -185,7 +185,9 @@ struct Epilogue {
           a.K2[o] = k;
           put_v_shift(a, b, i, scx[g], a.tr.c32[b] * k);
         } else if (PH == E_B3) {
-          a.K3[o] = k;
+          // stage 4 needs K1..K3 only in the error: their part of it, in the
+          // order the full sum takes them (the same roundings)
+          a.E3[o] = fma(kE3, k, fma(kE2, k2[g], kE1 * k1[g]));
           const double xn = fma(a.tr.hs[b], fma(kB3, k, fma(kB2, k2[g], kB1 * k1[g])), x[g]);
           a.X[(1 - xs[g]) * slot + o] = xn;
           float sn, cn;
@@ -194,7 +196,7 @@ struct Epilogue {
           a.SCX[(1 - xs[g]) * slot + o] = make_float2(sn, cn);   // X' (the state after acceptance)
         } else {
           a.K14[(1 - ks[g]) * slot + o] = k;
-          const double dv = a.tr.hs[b] * fma(kE4, k, fma(kE3, k3[g], fma(kE2, k2[g], kE1 * k1[g])));
+          const double dv = a.tr.hs[b] * fma(kE4, k, e3[g]);
           const double w = fmax(fmax(fabs(x[g]), fabs(y[g])), thr);
           double e = ratio(fabs(dv), w);
           if (!finite_bits(y[g]) || !finite_bits(k)) e = __longlong_as_double(0x7ff8000000000000ll);
@@ -362,7 +364,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   const size_t NN = (size_t)N * N, TN = (size_t)T * N;
   void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr, *vh1 = nullptr, *vl1 = nullptr, *scb = nullptr,
        *scx = nullptr;
-  double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *K3 = nullptr, *dsc = nullptr;
+  double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *E3 = nullptr, *dsc = nullptr;
   int *isc = nullptr, *derr = nullptr;
   long long* lsc = nullptr;
   unsigned long long* usc = nullptr;
@@ -399,7 +401,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaMalloc(&X, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K14, 2 * TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&K2, TN * sizeof(double)));
-  EN_CUDA(cudaMalloc(&K3, TN * sizeof(double)));
+  EN_CUDA(cudaMalloc(&E3, TN * sizeof(double)));
   EN_CUDA(cudaMalloc(&dsc, 6 * T * sizeof(double)));
   EN_CUDA(cudaMalloc(&isc, (6 * T + 1) * sizeof(int)));
   EN_CUDA(cudaMalloc(&lsc, 3 * T * sizeof(long long)));
@@ -434,7 +436,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   a.X = X;
   a.K14 = K14;
   a.K2 = K2;
-  a.K3 = K3;
+  a.E3 = E3;
   a.Vh = (__nv_bfloat16*)vh;
   a.Vl = (__nv_bfloat16*)vl;
   a.SC = (float2*)scb;
@@ -532,7 +534,7 @@ done:
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (graph) cudaGraphDestroy(graph);
-  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(scx); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(K3);
+  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(scx); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(E3);
   cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
   return rc;
 }
