@@ -63,6 +63,59 @@ struct EArgs {
   long long max_attempts, max_rejects;
 };
 
+// Conversions between binary32 and binary64 and the magnitude/maximum of
+// binary64 values by integer operations on the IEEE 754 encodings: on GB300
+// every binary64 instruction, conversions and fmax included, issues at the
+// binary64 rate, integer operations at the full rate.  The conversions are
+// exact (binary32 results rounded to nearest even, as the conversion
+// instruction rounds) for normal binary32 values; zeros, subnormals,
+// infinities and NaN, rare here, take the conversion instruction.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e - 1u >= 254u) return (double)f;
+  // exponent rebiased by 1023 - 127; the 23 fraction bits lead the 52
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  // normal binary32 results: binary64 exponents 897 .. 1150 (a carry out of
+  // the top binade rounds to infinity, as it should)
+  if (e - 897u > 253u) return (float)d;
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  // drop 29 fraction bits, rounding to nearest, ties to even
+  const unsigned long long r = mag + 0x0fffffffull + ((mag >> 29) & 1ull);
+  const unsigned fb = (unsigned)(r >> 29) - (896u << 23);
+  return __uint_as_float(fb | ((unsigned)(b >> 32) & 0x80000000u));
+}
+
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffll);
+}
+
+// max of two non-negative binary64 values (their encodings order as integers;
+// a NaN operand, whose encoding lies above +Inf, is returned)
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
+// sin and cos of a binary64 phase, rounded to binary32: the reduction of the
+// solver's sincos_f_of_d (two-constant Cody-Waite on 2 pi in binary64), with
+// the reduced phase converted by d2f
+__device__ __forceinline__ void sincos_phase(double th, float* s, float* c) {
+  const double kInv2Pi = 0.15915494309189535;
+  const double k2PiHi = 6.2831853069365025;             // 2 pi rounded to 33 bits
+  const double k2PiLo = 2.430840202602477e-10;           // 2 pi - k2PiHi
+  const double k = rint(th * kInv2Pi);
+  double r = fma(-k, k2PiHi, th);
+  r = fma(-k, k2PiLo, r);
+  sincosf(d2f(r), s, c);
+}
+
 constexpr double kB1 = 2.0 / 9.0, kB2 = 1.0 / 3.0, kB3 = 4.0 / 9.0;
 constexpr double kE1 = -5.0 / 72.0, kE2 = 1.0 / 12.0, kE3 = 1.0 / 9.0, kE4 = -1.0 / 8.0;
 
@@ -79,7 +132,7 @@ __device__ __forceinline__ void put_sc(const EArgs& a, int b, int i, float s, fl
 
 __device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
   float s, c;
-  sincos_f_of_d(y, &s, &c);
+  sincos_phase(y, &s, &c);
   put_sc(a, b, i, s, c);
 }
 
@@ -89,7 +142,7 @@ __device__ __forceinline__ void put_v(const EArgs& a, int b, int i, double y) {
 // costs five binary64 operations, this two).
 __device__ __forceinline__ void put_v_shift(const EArgs& a, int b, int i, float2 scx, double delta) {
   float sd, cd;
-  sincosf((float)delta, &sd, &cd);
+  sincosf(d2f(delta), &sd, &cd);
   const float s = fmaf(scx.x, cd, scx.y * sd);
   const float c = fmaf(scx.y, cd, -(scx.x * sd));
   put_sc(a, b, i, s, c);
@@ -118,9 +171,9 @@ __device__ __forceinline__ double warp_max(double v) {
 // Newton step in binary64 (relative error ~1e-14; three binary64 operations
 // instead of a correctly rounded division).  Outside [1e-30, 1e30] it divides.
 __device__ __forceinline__ double ratio(double n, double d) {
-  const float df = (float)d;
+  const float df = d2f(d);
   if (!(df >= 1e-30f && df <= 1e30f)) return n / d;   // (the range test in binary32)
-  const double r0 = (double)__frcp_rn(df);
+  const double r0 = f2d(__frcp_rn(df));
   return n * (r0 * fma(-d, r0, 2.0));
 }
 
@@ -168,7 +221,7 @@ struct Epilogue {
         if (!live[g]) continue;   // uniform over the warp
         const size_t o = (size_t)b * N + i;
         const float cpl = sc[g].y * v[2 * j] - sc[g].x * v[2 * j + 1];
-        const double k = om[g] + (double)cpl;
+        const double k = om[g] + f2d(cpl);
         if (PH == E_K1) {
           a.K14[ks[g] * slot + o] = k;
           const double s = a.rtol * fmax(fabs(x[g]), thr);
@@ -191,14 +244,14 @@ struct Epilogue {
           const double xn = fma(a.tr.hs[b], fma(kB3, k, fma(kB2, k2[g], kB1 * k1[g])), x[g]);
           a.X[(1 - xs[g]) * slot + o] = xn;
           float sn, cn;
-          sincos_f_of_d(xn, &sn, &cn);
+          sincos_phase(xn, &sn, &cn);
           put_sc(a, b, i, sn, cn);
           a.SCX[(1 - xs[g]) * slot + o] = make_float2(sn, cn);   // X' (the state after acceptance)
         } else {
           a.K14[(1 - ks[g]) * slot + o] = k;
           const double dv = a.tr.hs[b] * fma(kE4, k, e3[g]);
-          const double w = fmax(fmax(fabs(x[g]), fabs(y[g])), thr);
-          double e = ratio(fabs(dv), w);
+          const double w = max_nonneg(max_nonneg(abs_bits(x[g]), abs_bits(y[g])), thr);
+          double e = ratio(abs_bits(dv), w);
           if (!finite_bits(y[g]) || !finite_bits(k)) e = __longlong_as_double(0x7ff8000000000000ll);
           const double m = warp_max(e);
           if (lane == 0) atomicMax(&a.tr.emax[b], (unsigned long long)__double_as_longlong(m));
@@ -238,7 +291,7 @@ __global__ void ens_prologue(EArgs a, int which) {
     const double x = a.X[xs * slot + e];
     if (which == 0) {
       float s0, c0;
-      sincos_f_of_d(x, &s0, &c0);
+      sincos_phase(x, &s0, &c0);
       put_sc(a, b, i, s0, c0);
       a.SCX[xs * slot + e] = make_float2(s0, c0);   // the initial state's pair
     } else {
