@@ -129,7 +129,7 @@ def test_invalid_arguments_are_rejected():
     assert bs3.bs3_set_tuning(h, bs3.TUNE_RESIDENT_WEIGHTS, 2) == bs3.ERR_INVALID_ARG
     assert bs3.bs3_set_coupling(h, np.zeros((40, 40), np.float32), bs3.BF16, bs3.F32, False) == bs3.ERR_INVALID_ARG
     sysm.close()
-    # ensembles: T must fill whole 256-column tiles, N whole 128-row tiles
+    # ensembles: T must fill whole 128-column tiles (64 trajectories), N whole 128-row tiles
     torch = torch_cuda()
     for N, T in ((256, 100), (200, 128)):
         K = torch.zeros((N, N), dtype=torch.float32, device="cuda")
