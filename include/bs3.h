@@ -278,6 +278,18 @@ int bs3_set_proposer(bs3_system_t sys, const float* model);
  * Returns BS3_ERR_DEVICE_WAIT if a bounded pipeline wait ran out. */
 int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C);
 
+/* The same split product computed the way the ensembles' stage products run
+ * (bs3_ensemble_solve): persistent CTAs, at most one per SM (and at most
+ * max_ctas when max_ctas > 0), CTA b taking the 128 x tile_n output tiles b,
+ * b + grid, ... (numbered row block by row block), with two accumulators in
+ * tensor memory so that one tile's read-out overlaps the next tile's
+ * products; 16 epilogue warps store the binary32 accumulators.  Arguments as
+ * bs3_tc_gemm; tile_n = 128 or 256 with Nc % tile_n == 0.  Waits for
+ * completion.  Returns BS3_ERR_DEVICE_WAIT if a bounded pipeline wait ran out.
+ * The paper has no counterpart (the ensembles are the build's extension). */
+int bs3_tc_gemm_persistent(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C,
+                           int tile_n, int max_ctas);
+
 /* Lock-step ensemble of T Kuramoto trajectories sharing one coupling matrix
  * (the build's batched extension): theta_b' = omega_b + sum_j K_ij sin(theta_bj
  * - theta_bi), b = 0..T-1, each trajectory with its own adaptive h, t and
@@ -339,6 +351,67 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
                     const double* y0, const double* t0, const double* t1, double rtol, double atol, int variant,
                     int accum, double* y_final, bs3_stats* stats, double* kernel_ms, int device, void* stream);
 
+/* One instance of bs3_solve_batch: a system made by bs3_create_system with
+ * its weights stored (bs3_set_coupling), its initial state, span and
+ * tolerances; stats receives its counts and status. */
+typedef struct {
+    bs3_system_t sys;
+    const double* y0;             /* d*N initial state (memory kind per the call's flags) */
+    double* y_final;              /* d*N state at t_reached (same memory kind) */
+    double t0, t1;                /* t1 > t0 */
+    double rtol, atol;            /* Rel > 0, Ab >= 0 of Eq. ERROR-O23 for this instance */
+    bs3_stats stats;              /* out */
+} bs3_batch_item;
+
+/* A group of T Kuramoto trajectories that share one coupling matrix, solved
+ * by bs3_solve_batch beside the items as bs3_ensemble_solve solves it.  All
+ * pointers but the counts are device pointers: K N x N binary32 row-major,
+ * omega, theta0, theta_out [T][N] binary64.  n_acc, n_rej, status: host
+ * arrays of T (may be NULL).  ctas: CTAs of each stage product (0 = chosen by
+ * the call's cost model, see bs3_solve_batch); tile_n as
+ * bs3_ensemble_solve_tiled. */
+typedef struct {
+    const float* K;
+    int64_t N, T;
+    const double* omega;
+    const double* theta0;
+    double* theta_out;
+    double t0, t1, rtol, atol;
+    int tile_n;
+    int ctas;
+    int64_t* n_acc;
+    int64_t* n_rej;
+    int32_t* status;
+    int64_t lockstep_attempts;    /* out: lock-step attempts run */
+} bs3_ensemble_group;
+
+/* Solves a batch in one submission (the build's batched extension; the paper
+ * solves one system at a time): n_items independent systems, every one with
+ * its own span, tolerances, adaptive h and decisions, plus optionally (group
+ * != NULL) one shared-K trajectory group.  The items' systems must all be of
+ * one kind and one stored weight type, on `device`, with the Bogacki-Shampine
+ * pair (bs3_set_method), and circadian systems must share the eight
+ * constants.  variant and accum apply to every item (the group runs the
+ * tensor-core variant of bs3_ensemble_solve).  flags: BS3_HOST_IO if the
+ * items' y0 and y_final are host pointers.
+ *
+ * The items run as bs3_batch_solve runs its systems: one cooperative launch,
+ * largest systems first, systems too large for one SM's share solved by teams
+ * of CTAs, the others whole by single CTAs, each CTA taking systems from a work
+ * queue.  The group runs as one graph whose attempt loop is a conditional
+ * node decided on the device.  With both, the items' launch and the group's
+ * graph are one CUDA graph with two branches on disjoint CTA budgets: the group's
+ * products get group->ctas CTAs (0: SMs x its share of the estimated work per
+ * attempt, the tensor-core products at 1 PFLOP/s against the items' weight
+ * streams at 30 GB/s per CTA), the items the remaining SMs.  Items' weights
+ * are the systems' stored copies; the call allocates a small descriptor
+ * block and, once per system, a state buffer the system keeps.  Waits for
+ * completion; *kernel_ms (may be NULL) receives the device time of the
+ * solve.  Returns the first non-OK item status, else the group's, else
+ * BS3_OK; BS3_ERR_INVALID_ARG for mixed kinds, types or devices. */
+int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int accum, int flags,
+                    bs3_ensemble_group* group, int device, void* stream, double* kernel_ms);
+
 /* Largest N accepted by bs3_solve_noalloc. */
 #define BS3_NOALLOC_MAX_N 16384
 
@@ -353,32 +426,47 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
  * sums, row scales, k1/(k0-k1) and the control block for N <= 16384), which
  * every GPU that loads the library holds until the process exits.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress)
- * with the device current; make that first call before any stream capture.
- * All calls share the array and every call overwrites it, so calls that
- * overlap on the GPU (other streams, other host threads) race: serialise them.
- * No cudaMalloc, cudaFree or allocating library routine is called.
+ * with the device current.  All calls share the array and every call
+ * overwrites it, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The call is synchronous: it waits for the
+ * solve and reads its control block back, so it cannot be called while the
+ * stream is being captured into a CUDA graph.
  *
  * Arguments (all arrays are device pointers of the current device unless noted):
  *   kind, N       as bs3_create_system; 1 <= N <= BS3_NOALLOC_MAX_N;
  *   par           N per-agent values (omega_i or k1_i; NULL for BS3_LCO_PAPER);
  *   globals       host array of the 8 circadian constants k0, k2, k3, a, b, c,
- *                 eps, I0 (NULL for the other kinds);
+ *                 eps, I0 (NULL for the other kinds); k0 finite and > 0, and
+ *                 every k1_i in (0, k0), as bs3_create_system requires;
  *   weights, store, ld
  *                 the coupling weights already in their stored form: N rows of
  *                 ld values of type store (BS3_F32 or BS3_F64, row scale 1),
- *                 ld a multiple of 16 and >= N, columns N..ld-1 equal to zero,
- *                 16-byte aligned;
+ *                 ld a multiple of 16 with N <= ld <= BS3_NOALLOC_MAX_N,
+ *                 columns N..ld-1 equal to zero, 16-byte aligned;
  *   the rest      as bs3_solve with device pointers (t_out ascending within
  *                 [t0, t1]), stats on the host, stream a cudaStream_t or NULL.
  * The failure limits are bs3_default_limits() except the wall-clock ones,
  * which need host-mapped memory and are not enforced.  Returns the solve
- * status after the results are complete; BS3_ERR_INVALID_ARG for N above
- * BS3_NOALLOC_MAX_N or a malformed argument. */
+ * status after the results are complete (also in stats->status);
+ * BS3_ERR_INVALID_ARG for N or ld above BS3_NOALLOC_MAX_N or a malformed
+ * argument, before anything is launched (the circadian k1 check runs on the
+ * device and returns before the solve); BS3_ERR_CUDA if a CUDA call fails. */
 int bs3_solve_noalloc(int kind, int64_t N, const double* par, const double* globals,
                       const void* weights, int store, int64_t ld, double t0, double t1,
                       const double* y0, double rtol, double atol, int variant, int accum,
                       const double* t_out, int64_t n_out, double* y_out, double* final_y,
                       bs3_stats* stats, void* stream);
+
+/* Read-bandwidth probe (measurement only; the paper has no counterpart): one
+ * untimed pass, then `reps` passes over `bytes` of device memory at buf
+ * (16-byte aligned, bytes a multiple of 16) with the coupling pass's loads
+ * (16-byte, non-allocating in L1, L2 evict_last), two 512-thread CTAs per SM
+ * each reading a contiguous share; *gbs_out receives bytes * reps / time in
+ * GB/s (CUDA events on the legacy default stream).  A buffer that fits in L2
+ * gives the L2 read rate that bounds a coupling pass whose weights stay
+ * there.  Errors: BS3_ERR_INVALID_ARG for a bad buffer, size or count. */
+int bs3_read_bandwidth(const void* buf, int64_t bytes, int reps, double* gbs_out);
 
 /* Frees the system and everything it owns.  NULL is allowed. */
 int bs3_destroy_system(bs3_system_t sys);

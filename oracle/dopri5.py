@@ -6,7 +6,7 @@ is a plain restatement: tableau of oracle.tableau (Dormand & Prince 1980),
 local extrapolation (the fifth-order solution is kept), FSAL, the error norm
 sqrt(mean((err_k / (atol + rtol max(|y_k|, |ynew_k|)))^2)), and the standard
 controller h <- h min(5, max(0.2, 0.9 err^(-1/5))).  Pinned against closed
-forms and against scipy's RK45 in tests/test_oracle_reference.py.
+forms and against scipy's RK45 in tests/test_oracle_solver.py.
 """
 
 from __future__ import annotations

@@ -65,6 +65,7 @@ class System:
     globals: Optional[Dict[str, float]] = None
     rowsum: Optional[np.ndarray] = None   # lco_paper: sum_j s_i q_ij (float64)
     theta_h: Optional[np.ndarray] = None  # circadian: k1/(k0-k1) (float64)
+    ksplit: Optional[tuple] = None        # tensor variant: bfloat16 split of q (computed once)
 
     @property
     def d(self) -> int:
@@ -229,16 +230,30 @@ def split_bf16(x32: np.ndarray):
     return hi.astype(F64), lo.astype(F64)
 
 
-def rhs_tensor(sysm: System, t: float, y: np.ndarray) -> np.ndarray:
+def tensor_sums(sysm: System, y: np.ndarray):
+    """The split products of the tensor-core variant: S_i = sum_j (K_hi s_hi
+    + K_hi s_lo + K_lo s_hi)_ij and C_i likewise with cos, summed in binary64
+    (every product of two bfloat16 values is exact there) and rounded once to
+    binary32; also the binary32 sin/cos of the phases.  Returns (S, C, s, c)."""
     if sysm.kind != "kuramoto":
         raise ValueError("the tensor-core variant is defined for Kuramoto ensembles")
-    kh, kl = split_bf16(sysm.q.astype(F32))
+    if sysm.ksplit is None:
+        sysm.ksplit = split_bf16(sysm.q.astype(F32))
+    kh, kl = sysm.ksplit
     th = np.asarray(y, dtype=F64)
     sj, cj = np.sin(th).astype(F32), np.cos(th).astype(F32)
-    sh, sl = split_bf16(sj)
-    ch, cl = split_bf16(cj)
-    S = (kh @ sh + kh @ sl + kl @ sh).astype(F32)
-    C = (kh @ ch + kh @ cl + kl @ ch).astype(F32)
+    vh, vl = split_bf16(np.stack([sj, cj], axis=1))     # columns: sine, cosine
+    SC = kh @ vh + kh @ vl + kl @ vh
+    S = SC[:, 0].astype(F32)
+    C = SC[:, 1].astype(F32)
+    return S, C, sj, cj
+
+
+def rhs_tensor(sysm: System, t: float, y: np.ndarray) -> np.ndarray:
+    """Kuramoto right-hand side of the tensor-core variant: the i-side finish
+    cos(theta_i) S_i - sin(theta_i) C_i in binary32, then omega_i + coupling in
+    binary64."""
+    S, C, sj, cj = tensor_sums(sysm, y)
     coupling = cj * S - sj * C
     return sysm.params + coupling.astype(F64)
 

@@ -38,7 +38,8 @@ EXPORTED = (
     "bs3_set_history", "bs3_get_history", "bs3_set_tuning", "bs3_solve_noalloc",
     "bs3_mlp_dataset", "bs3_mlp_train", "bs3_mlp_grad", "bs3_set_proposer", "bs3_tc_gemm",
     "bs3_ensemble_solve", "bs3_batch_solve", "bs3_autotune", "bs3_set_method",
-    "bs3_ensemble_solve_tiled", "bs3_ensemble_autotune",
+    "bs3_ensemble_solve_tiled", "bs3_ensemble_autotune", "bs3_tc_gemm_persistent",
+    "bs3_read_bandwidth", "bs3_solve_batch",
 )
 METHOD_BS32, METHOD_DP54 = 0, 1
 METHOD_IDS = {"bs32": METHOD_BS32, "dp54": METHOD_DP54}
@@ -73,6 +74,40 @@ class bs3_limits(ctypes.Structure):
     ]
 
 
+class bs3_batch_item(ctypes.Structure):
+    _fields_ = [
+        ("sys", ctypes.c_void_p),
+        ("y0", ctypes.c_void_p),
+        ("y_final", ctypes.c_void_p),
+        ("t0", ctypes.c_double),
+        ("t1", ctypes.c_double),
+        ("rtol", ctypes.c_double),
+        ("atol", ctypes.c_double),
+        ("stats", bs3_stats),
+    ]
+
+
+class bs3_ensemble_group(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_void_p),
+        ("N", ctypes.c_int64),
+        ("T", ctypes.c_int64),
+        ("omega", ctypes.c_void_p),
+        ("theta0", ctypes.c_void_p),
+        ("theta_out", ctypes.c_void_p),
+        ("t0", ctypes.c_double),
+        ("t1", ctypes.c_double),
+        ("rtol", ctypes.c_double),
+        ("atol", ctypes.c_double),
+        ("tile_n", ctypes.c_int),
+        ("ctas", ctypes.c_int),
+        ("n_acc", ctypes.c_void_p),
+        ("n_rej", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+        ("lockstep_attempts", ctypes.c_int64),
+    ]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -104,6 +139,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "bs3_mlp_grad": (I, [P, P, P, I64, P, P]),
         "bs3_set_proposer": (I, [P, P]),
         "bs3_tc_gemm": (I, [I64, I64, I64, P, P, P]),
+        "bs3_tc_gemm_persistent": (I, [I64, I64, I64, P, P, P, I, I]),
+        "bs3_read_bandwidth": (I, [P, I64, I, ctypes.POINTER(D)]),
+        "bs3_solve_batch": (I, [P, I64, I, I, I, ctypes.POINTER(bs3_ensemble_group), I, P, ctypes.POINTER(D)]),
         "bs3_ensemble_solve": (I, [P, I64, I64, P, P, D, D, D, D, P, P, P, P, ctypes.POINTER(I64), P]),
         "bs3_batch_solve": (I, [I, I64, P, P, P, I, P, P, P, D, D, I, I, P, P, ctypes.POINTER(D), I, P]),
         "bs3_autotune": (I, [P, P, D, D, D, I, I, I, P, ctypes.POINTER(D)]),
@@ -261,6 +299,10 @@ def bs3_tc_gemm(M: int, Nc: int, K: int, A, B, C) -> int:
     return load().bs3_tc_gemm(M, Nc, K, _ptr(A), _ptr(B), _ptr(C))
 
 
+def bs3_tc_gemm_persistent(M: int, Nc: int, K: int, A, B, C, tile_n: int = 128, max_ctas: int = 0) -> int:
+    return load().bs3_tc_gemm_persistent(M, Nc, K, _ptr(A), _ptr(B), _ptr(C), tile_n, max_ctas)
+
+
 def bs3_ensemble_solve(K, N: int, T: int, omega, theta0, t0: float, t1: float, rtol: float, atol: float,
                        theta_out, stream: int = 0, tile_n: int = 0, max_lockstep: int = 0):
     """Returns (rc, n_acc[T], n_rej[T], status[T], lockstep_attempts)."""
@@ -309,6 +351,41 @@ def bs3_autotune(sys_: int, y0, t0: float, t1: float, rtol: float, variant: int,
     us = ctypes.c_double()
     rc = load().bs3_autotune(sys_, _ptr(y0), t0, t1, rtol, variant, accum, attempts, _ptr(choice), ctypes.byref(us))
     return rc, (int(choice[0]), int(choice[1])), us.value
+
+
+def bs3_solve_batch(items, variant: int, accum: int, flags: int = 0, group=None, device: int = 0,
+                    stream: int = 0):
+    """items: a sequence of dicts with keys sys (handle), y0, y_final (pointers or arrays), t0, t1, rtol,
+    atol; group: None or a dict with the fields of bs3_ensemble_group (pointers/arrays, n_acc etc. numpy
+    arrays).  Returns (rc, [bs3_stats per item], lockstep attempts of the group or None, kernel ms)."""
+    n = len(items)
+    arr = (bs3_batch_item * max(n, 1))()
+    for k, it in enumerate(items):
+        arr[k].sys = it["sys"]
+        arr[k].y0 = _ptr(it["y0"])
+        arr[k].y_final = _ptr(it["y_final"])
+        arr[k].t0, arr[k].t1 = it["t0"], it["t1"]
+        arr[k].rtol, arr[k].atol = it["rtol"], it["atol"]
+    g = None
+    if group is not None:
+        g = bs3_ensemble_group()
+        for f in ("K", "omega", "theta0", "theta_out", "n_acc", "n_rej", "status"):
+            setattr(g, f, _ptr(group.get(f)))
+        for f in ("N", "T", "t0", "t1", "rtol", "atol"):
+            setattr(g, f, group[f])
+        g.tile_n = group.get("tile_n", 0)
+        g.ctas = group.get("ctas", 0)
+    ms = ctypes.c_double()
+    rc = load().bs3_solve_batch(ctypes.cast(arr, ctypes.c_void_p), n, variant, accum, flags,
+                                None if g is None else ctypes.byref(g), device, stream or None, ctypes.byref(ms))
+    return rc, [arr[k].stats for k in range(n)], (None if g is None else g.lockstep_attempts), ms.value
+
+
+def bs3_read_bandwidth(buf, nbytes: int, reps: int):
+    """Returns (rc, GB/s)."""
+    gbs = ctypes.c_double()
+    rc = load().bs3_read_bandwidth(_ptr(buf), nbytes, reps, ctypes.byref(gbs))
+    return rc, gbs.value
 
 
 def bs3_destroy_system(sys_: int) -> int:

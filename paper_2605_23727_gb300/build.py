@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbs3.so")
 
-SOURCES = ["bs3_api.cu", "bs3_noalloc.cu", "bs3_mlp.cu", "bs3_tc.cu", "bs3_ensemble.cu"] + sorted(f for f in os.listdir(CSRC) if f.startswith("inst_") and f.endswith(".cu"))
+SOURCES = ["bs3_api.cu", "bs3_noalloc.cu", "bs3_mlp.cu", "bs3_tc.cu", "bs3_ensemble.cu", "bs3_probe.cu"] + sorted(f for f in os.listdir(CSRC) if f.startswith("inst_") and f.endswith(".cu"))
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [

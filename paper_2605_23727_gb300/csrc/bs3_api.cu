@@ -17,6 +17,7 @@
 
 #include "../../include/bs3.h"
 #include "bs3_device.cuh"
+#include "bs3_ensemble.h"
 #include "bs3_kernels.h"
 #include "bs3_mlp.cuh"
 #include "bs3_solver.cuh"
@@ -69,6 +70,7 @@ struct bs3_system {
   bool mlp_on = false;
   int mlp_off = 0;
   int grid_store = -1;
+  double* bstate = nullptr;    // [6][d][N] state slots of the system in a batch (bs3_solve_batch), on first use
 };
 
 namespace {
@@ -238,7 +240,7 @@ int pick_grid(bs3_system* s) {
   const bool resident = s->kind != BS3_CIRCADIAN && s->allow_resident && slab + state + mlp <= budget;
   const size_t smem = (resident ? slab : 0) + state + mlp;
   s->mlp_off = (int)((resident ? slab : 0) + state);
-  BS3_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BS3_CUDA(allow_max_smem(k, s->device));
   int nb = 0;
   BS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, smem));
   if (nb < 1) return BS3_ERR_CUDA;
@@ -571,6 +573,8 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
       D.ctrl = (Control*)(arena + oCtl) + k;
       D.t0 = t0[k];
       D.t1 = t1[k];
+      D.rtol = rtol;
+      D.atol = atol;
     }
     if (cudaMemcpyAsync(arena + oDesc, desc.data(), S * sizeof(SysDesc), cudaMemcpyHostToDevice, st) !=
         cudaSuccess) { rc = BS3_ERR_CUDA; break; }
@@ -808,6 +812,7 @@ int bs3_destroy_system(bs3_system_t s) {
   cudaFree(s->stage_out);
   cudaFree(s->hist);
   cudaFree(s->mlp);
+  cudaFree(s->bstate);
   if (s->cancel_h) cudaFreeHost(s->cancel_h);
   if (s->progress_h) cudaFreeHost(s->progress_h);
   delete s;
@@ -1028,6 +1033,266 @@ int bs3_solve(bs3_system_t s, double t0, double t1, const double* y0, double rto
     stats->n_out_written = (int32_t)c.n_out;
   }
   return c.status;
+}
+
+int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int accum, int flags,
+                    bs3_ensemble_group* group, int device, void* stream_, double* kernel_ms) {
+  if (n_items < 0 || (n_items > 0 && !items) || (n_items == 0 && !group) || n_items > (1 << 24))
+    return BS3_ERR_INVALID_ARG;
+  if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64)
+    return BS3_ERR_INVALID_ARG;
+  const bool host_io = (flags & BS3_HOST_IO) != 0;
+  for (int64_t k = 0; k < n_items; ++k) {
+    bs3_batch_item& it = items[k];
+    std::memset(&it.stats, 0, sizeof(it.stats));
+    it.stats.status = BS3_ERR_INVALID_ARG;
+  }
+  // the items: one kind, one stored type, one device, the 3(2) pair, shared circadian constants
+  const bs3_system* s0 = n_items > 0 ? items[0].sys : nullptr;
+  for (int64_t k = 0; k < n_items; ++k) {
+    const bs3_batch_item& it = items[k];
+    const bs3_system* s = it.sys;
+    if (!s || s->store < 0 || !it.y0 || !it.y_final || !(it.t1 > it.t0) || !std::isfinite(it.t0) ||
+        !std::isfinite(it.t1) || !(it.rtol > 0.0) || !(it.atol >= 0.0))
+      return BS3_ERR_INVALID_ARG;
+    if (s->kind != s0->kind || s->store != s0->store || s->device != device || s->method != BS3_METHOD_BS32)
+      return BS3_ERR_INVALID_ARG;
+    if (s->kind == BS3_CIRCADIAN)
+      for (int q = 0; q < 8; ++q)
+        if (s->g[q] != s0->g[q]) return BS3_ERR_INVALID_ARG;
+  }
+  if (group && (!group->K || !group->omega || !group->theta0 || !group->theta_out || group->ctas < 0))
+    return BS3_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  const int64_t S = n_items;
+  int sms = 0;
+  BS3_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  cudaStream_t st = (cudaStream_t)stream_, own = nullptr, side = nullptr, body = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  EnsembleRun* run = nullptr;
+  unsigned char* arena = nullptr;
+  int rc = BS3_OK;
+  // CTA budgets: the group's stage products and the items' cooperative launch
+  int g_ctas = 0, i_ctas = sms;
+  std::vector<int64_t> order(S);
+  std::vector<SysDesc> desc(S);
+  std::vector<Control> ctl(S);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
+  const size_t oDesc = take((size_t)std::max<int64_t>(S, 1) * sizeof(SysDesc)),
+               oCtl = take((size_t)std::max<int64_t>(S, 1) * sizeof(Control)), oNext = take(sizeof(int)),
+               oBigNext = take(sizeof(int)), oTeamJob = take(kMaxTeams * sizeof(int)),
+               oTeamBar = take(kMaxTeams * sizeof(unsigned long long)), oTeamStatus = take(kMaxTeams * sizeof(int));
+  BatchArgs ba;
+  std::memset(&ba, 0, sizeof(ba));
+  const void* bkern = S > 0 ? batch_kernel_lookup(s0->kind, s0->store) : nullptr;
+  do {
+    if (st == nullptr) {   // graphs cannot be captured on the legacy default stream
+      if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaDeviceSynchronize() != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      st = own;
+    }
+    if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    if (group && S > 0) {
+      if (group->ctas > 0) {
+        g_ctas = std::min(group->ctas, sms - 1);
+      } else {
+        // estimated work per attempt: the group's three split-product stages
+        // at ~1 PFLOP/s, each item's three weight streams at ~30 GB/s per CTA
+        const double g_us = 9.0 * 2.0 * (double)group->N * group->N * 2.0 * group->T / 1.0e9;
+        double i_us = 0.0;
+        for (int64_t k = 0; k < S; ++k) {
+          const double n = (double)items[k].sys->N;
+          i_us += kAttemptFixedUs + 3.0 * n * n * (double)store_bytes(s0->store) / kCtaStreamBytesPerUs;
+        }
+        i_us /= sms;   // the items spread over the SMs
+        g_ctas = (int)std::lround(sms * g_us / (g_us + i_us));
+      }
+      g_ctas = std::max(1, std::min(g_ctas, sms - 1));
+      i_ctas = sms - g_ctas;
+    } else if (group) {
+      g_ctas = group->ctas > 0 ? std::min(group->ctas, sms) : sms;
+    }
+    // ---- the items: initial states, descriptors (largest first), plan
+    if (S > 0) {
+      for (int64_t k = 0; k < S; ++k) {
+        bs3_system* s = items[k].sys;
+        const size_t dN = (size_t)s->d * s->N;
+        if (!s->bstate && cudaMalloc(&s->bstate, 6 * dN * sizeof(double)) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+        if (cudaMemcpyAsync(s->X, items[k].y0, dN * sizeof(double),
+                            host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+          rc = BS3_ERR_CUDA;
+          break;
+        }
+      }
+      if (rc != BS3_OK) break;
+      if (cudaMalloc(&arena, off) != cudaSuccess || cudaMemsetAsync(arena, 0, off, st) != cudaSuccess) {
+        rc = BS3_ERR_CUDA;
+        break;
+      }
+      for (int64_t k = 0; k < S; ++k) order[k] = k;
+      std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return items[x].sys->N > items[y].sys->N; });
+      std::vector<int64_t> sortedN(S);
+      for (int64_t r = 0; r < S; ++r) {
+        const bs3_batch_item& it = items[order[r]];
+        const bs3_system* s = it.sys;
+        SysDesc& D = desc[r];
+        D.N = (int)s->N;
+        D.ld = (int)s->ld;
+        D.q = s->q;
+        D.scale = s->scale;
+        D.rowsum = s->rowsum;
+        D.par = s->par;
+        D.theta_h = s->theta_h;
+        D.y0 = s->X;
+        D.y_final = s->Xn;
+        D.state = s->bstate;
+        D.jv32 = s->jv32;
+        D.jv64 = s->jv64;
+        D.ctrl = (Control*)(arena + oCtl) + order[r];
+        D.t0 = it.t0;
+        D.t1 = it.t1;
+        D.rtol = it.rtol;
+        D.atol = it.atol;
+        sortedN[r] = s->N;
+      }
+      if (cudaMemcpyAsync(arena + oDesc, desc.data(), S * sizeof(SysDesc), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      Args& a = ba.common;
+      a.variant = variant;
+      a.accum = accum;
+      a.rtol = 1.0;
+      a.atol = 1.0;
+      a.hmin = 100.0 * (variant == BS3_SINGLE ? (double)FLT_EPSILON : DBL_EPSILON);
+      a.max_attempts = 100000;
+      a.max_rejects = 85000;
+      a.spin_limit = (long long)1 << 26;
+      a.l2_keep = 0;
+      a.method = M_BS32;
+      a.n_slots = 6;
+      for (int q = 0; q < 8; ++q) a.g[q] = s0->g[q];
+      ba.sys = (const SysDesc*)(arena + oDesc);
+      ba.S = (int)S;
+      ba.next = (int*)(arena + oNext);
+      ba.big_next = (int*)(arena + oBigNext);
+      ba.team_job = (int*)(arena + oTeamJob);
+      ba.team_bar = (unsigned long long*)(arena + oTeamBar);
+      ba.team_status = (int*)(arena + oTeamStatus);
+      const BatchPlan plan = plan_batch(sortedN, i_ctas, store_bytes(s0->store));
+      ba.n_big = plan.n_big;
+      ba.team = plan.team;
+      ba.n_teams = plan.n_teams;
+      i_ctas = plan.grid;
+    }
+    // ---- the group's buffers and initial state
+    if (group) {
+      const EnsembleSpec sp{group->K, group->N, group->T, group->omega, group->theta0, group->t0, group->t1,
+                            group->rtol, group->atol, group->tile_n, 0, g_ctas, group->theta_out};
+      rc = ensemble_create(sp, st, &run);
+      if (rc != BS3_OK) break;
+      if (cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    }
+    // ---- one submission
+    void* kargs[] = {&ba};
+    cudaLaunchAttribute coop;
+    coop.id = cudaLaunchAttributeCooperative;
+    coop.val.cooperative = 1;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)i_ctas);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.attrs = &coop;
+    cfg.numAttrs = 1;
+    if (!group) {
+      cfg.stream = st;
+      if (cudaEventRecord(ev0, st) != cudaSuccess || cudaLaunchKernelExC(&cfg, bkern, kargs) != cudaSuccess ||
+          cudaEventRecord(ev1, st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    } else {
+      if (S > 0 && (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
+        rc = BS3_ERR_CUDA;
+        break;
+      }
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      cudaError_t ce = cudaSuccess;
+      if (S > 0) {
+        // the items' launch on a branch of its own
+        ce = cudaEventRecord(fork, st);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(side, fork, 0);
+        cfg.stream = side;
+        if (ce == cudaSuccess) ce = cudaLaunchKernelExC(&cfg, bkern, kargs);
+        if (ce == cudaSuccess) ce = cudaEventRecord(join, side);
+      }
+      int crc = ce == cudaSuccess ? run->capture(st, body, nullptr, nullptr) : BS3_ERR_CUDA;
+      if (S > 0 && crc == BS3_OK && cudaStreamWaitEvent(st, join, 0) != cudaSuccess) crc = BS3_ERR_CUDA;
+      const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+      if (crc != BS3_OK || ee != cudaSuccess) { rc = crc != BS3_OK ? crc : BS3_ERR_CUDA; break; }
+      if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess || cudaEventRecord(ev0, st) != cudaSuccess ||
+          cudaGraphLaunch(exec, st) != cudaSuccess || cudaEventRecord(ev1, st) != cudaSuccess) {
+        rc = BS3_ERR_CUDA;
+        break;
+      }
+    }
+    if (cudaEventSynchronize(ev1) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    if (kernel_ms) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      *kernel_ms = ms;
+    }
+    // ---- results
+    int worst = BS3_OK;
+    if (S > 0) {
+      std::vector<int> team_status(kMaxTeams, 0);
+      if (cudaMemcpyAsync(ctl.data(), arena + oCtl, S * sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(team_status.data(), arena + oTeamStatus, kMaxTeams * sizeof(int), cudaMemcpyDeviceToHost,
+                          st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      for (int64_t k = 0; k < S && rc == BS3_OK; ++k) {
+        const bs3_system* s = items[k].sys;
+        if (cudaMemcpyAsync(items[k].y_final, s->Xn, (size_t)s->d * s->N * sizeof(double),
+                            host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+          rc = BS3_ERR_CUDA;
+      }
+      if (rc != BS3_OK || cudaStreamSynchronize(st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      for (int64_t k = 0; k < S; ++k) {
+        bs3_stats& o = items[k].stats;
+        o.n_accepted = ctl[k].n_acc;
+        o.n_rejected = ctl[k].n_rej;
+        o.n_rhs_evals = ctl[k].n_rhs;
+        o.t_reached = ctl[k].t;
+        o.h_last = ctl[k].h;
+        o.status = ctl[k].status;
+        o.n_out_written = 0;
+        if (ctl[k].status != BS3_OK && worst == BS3_OK) worst = ctl[k].status;
+      }
+      for (int t = 0; t < kMaxTeams; ++t)
+        if (team_status[t] != 0 && worst == BS3_OK) worst = BS3_ERR_DEVICE_WAIT;
+    }
+    if (group) {
+      int64_t steps = 0;
+      const int grc = run->finish(group->n_acc, group->n_rej, group->status, &steps);
+      group->lockstep_attempts = steps;
+      if (grc != BS3_OK && worst == BS3_OK) worst = grc;
+    }
+    rc = worst;
+  } while (0);
+  if (own) cudaStreamSynchronize(own);
+  if (stream_) cudaStreamSynchronize((cudaStream_t)stream_);
+  delete run;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (side) cudaStreamDestroy(side);
+  if (body) cudaStreamDestroy(body);
+  if (own) cudaStreamDestroy(own);
+  cudaFree(arena);
+  return rc;
 }
 
 }  // extern "C"

@@ -33,6 +33,7 @@
 #include "bs3_device.cuh"
 #include "bs3_tc.cuh"
 #include "bs3_tc_host.h"
+#include "bs3_ensemble.h"
 
 namespace bs3 {
 namespace ens {
@@ -388,61 +389,89 @@ __global__ void ens_gather(EArgs a, double* out) {
 }  // namespace ens
 }  // namespace bs3
 
-using namespace bs3;
-using namespace bs3::ens;
+namespace bs3 {
+namespace ens {
 
-#define EN_CUDA(call)                                     \
-  do {                                                    \
-    if ((call) != cudaSuccess) { rc = BS3_ERR_CUDA; goto done; } \
-  } while (0)
-#define EN_RC(expr)                \
-  do {                             \
-    rc = (expr);                   \
-    if (rc != BS3_OK) goto done;   \
-  } while (0)
+// The attempt loop's condition: before the loop, whether any trajectory is
+// live; after each lock-step attempt, whether any still is, no bounded wait
+// ran out and the attempt bound is not reached.  One thread (concurrent
+// updates of a graph condition are undefined).
+__global__ void ens_loop_start(cudaGraphConditionalHandle h, const int* any_live, const int* err,
+                               long long* iters) {
+  *iters = 0;
+  cudaGraphSetConditional(h, (*any_live != 0 && *err == 0) ? 1u : 0u);
+}
+
+__global__ void ens_loop_next(cudaGraphConditionalHandle h, const int* any_live, const int* err, long long* iters,
+                              long long max_iters) {
+  const long long it = *iters + 1;
+  *iters = it;
+  cudaGraphSetConditional(h, (*any_live != 0 && *err == 0 && it < max_iters) ? 1u : 0u);
+}
+
+}  // namespace ens
+
+namespace {
+
+using namespace ens;
 
 template <int BNT>
-int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
-                        double t0, double t1, double rtol, double atol, int64_t max_lockstep, double* theta_out,
-                        int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts,
-                        void* stream_, float* loop_ms = nullptr) {
-  if (!K || !omega || !theta0 || !theta_out) return BS3_ERR_INVALID_ARG;
+class EnsembleRunT final : public EnsembleRun {
+ public:
+  ~EnsembleRunT() override {
+    cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb);
+    cudaFree(scx); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(E3);
+    cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr); cudaFree(iters);
+  }
+
+  int init(const EnsembleSpec& sp, cudaStream_t st);
+  int capture(cudaStream_t st, cudaStream_t body, cudaEvent_t loop_begin, cudaEvent_t loop_end) override;
+  int finish(int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts) override;
+  double flop_per_attempt() const override { return 3.0 * 3.0 * 2.0 * (double)N * (double)N * (double)(2 * T); }
+
+ private:
   using PT = tc::PTile<BNT>;
-  if (N < tc::BM || N % tc::BM || N % tc::BK || T < BNT / 2 || (2 * T) % BNT) return BS3_ERR_INVALID_ARG;
-  if (N > (1 << 20) || T > (1 << 16)) return BS3_ERR_INVALID_ARG;
-  if (!(t1 > t0) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream_;
-  cudaStream_t own = nullptr;   // graphs cannot be captured on the legacy default stream
-  int rc = BS3_OK;
-  const size_t NN = (size_t)N * N, TN = (size_t)T * N;
+  int64_t N = 0, T = 0, max_lockstep = 0;
+  double* theta_out = nullptr;
   void *kh = nullptr, *kl = nullptr, *vh = nullptr, *vl = nullptr, *vh1 = nullptr, *vl1 = nullptr, *scb = nullptr,
        *scx = nullptr;
   double *X = nullptr, *K14 = nullptr, *K2 = nullptr, *E3 = nullptr, *dsc = nullptr;
   int *isc = nullptr, *derr = nullptr;
-  long long* lsc = nullptr;
+  long long *lsc = nullptr, *iters = nullptr;
   unsigned long long* usc = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   CUtensorMap mAh, mAl, mBh, mBl, mBh1, mBl1;
   EArgs a;
-  std::memset(&a, 0, sizeof(a));
-  int herr = 0, any = 1;
-  long long iters = 0;
-  const int U = 8;   // attempts per graph launch
-  int dev = 0, sms = 0;   // (nothing is allocated yet)
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                 cudaSuccess)
-    return BS3_ERR_CUDA;
+  dim3 ggrid;
+  unsigned ctl_blocks = 1, ew_blocks = 1;
+  cudaStream_t stream = nullptr;
+};
+
+#define EN_CUDA(call)                                         \
+  do {                                                        \
+    if ((call) != cudaSuccess) return BS3_ERR_CUDA;           \
+  } while (0)
+#define EN_RC(expr)              \
+  do {                           \
+    const int rc_ = (expr);      \
+    if (rc_ != BS3_OK) return rc_; \
+  } while (0)
+
+template <int BNT>
+int EnsembleRunT<BNT>::init(const EnsembleSpec& sp, cudaStream_t st) {
+  N = sp.N;
+  T = sp.T;
+  max_lockstep = sp.max_lockstep;
+  theta_out = sp.theta_out;
+  stream = st;
+  const size_t NN = (size_t)N * N, TN = (size_t)T * N;
+  int dev = 0, sms = 0;
+  EN_CUDA(cudaGetDevice(&dev));
+  EN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t n_tiles = (N / tc::BM) * (2 * T / BNT);
-  const dim3 ggrid((unsigned)std::min<int64_t>(n_tiles, sms));
-  const unsigned ctl_blocks = (unsigned)((T + 255) / 256);
-  const unsigned ew_blocks = (unsigned)std::min<size_t>((TN + 255) / 256, 152 * 16);
-  if (st == nullptr) {
-    EN_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-    EN_CUDA(cudaDeviceSynchronize());   // the caller's legacy-stream work is complete
-    st = own;
-  }
+  const int cap = sp.max_ctas > 0 ? std::min(sp.max_ctas, sms) : sms;
+  ggrid = dim3((unsigned)std::min<int64_t>(n_tiles, cap));
+  ctl_blocks = (unsigned)((T + 255) / 256);
+  ew_blocks = (unsigned)std::min<size_t>((TN + 255) / 256, 152 * 16);
   EN_CUDA(cudaMalloc(&kh, NN * 2));
   EN_CUDA(cudaMalloc(&kl, NN * 2));
   EN_CUDA(cudaMalloc(&vh, 2 * TN * 2));
@@ -460,6 +489,7 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaMalloc(&lsc, 3 * T * sizeof(long long)));
   EN_CUDA(cudaMalloc(&usc, 4 * T * sizeof(unsigned long long)));
   EN_CUDA(cudaMalloc(&derr, sizeof(int)));
+  EN_CUDA(cudaMalloc(&iters, sizeof(long long)));
   EN_CUDA(cudaMemsetAsync(vh, 0, 2 * TN * 2, st));
   EN_CUDA(cudaMemsetAsync(vl, 0, 2 * TN * 2, st));
   EN_CUDA(cudaMemsetAsync(vh1, 0, 2 * TN * 2, st));
@@ -470,8 +500,9 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaMemsetAsync(lsc, 0, 3 * T * sizeof(long long), st));
   EN_CUDA(cudaMemsetAsync(usc, 0, 4 * T * sizeof(unsigned long long), st));
   EN_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), st));
-  EN_CUDA(cudaMemcpyAsync(X, theta0, TN * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  EN_RC(tc_split(K, NN, kh, kl, st));
+  EN_CUDA(cudaMemsetAsync(iters, 0, sizeof(long long), st));
+  EN_CUDA(cudaMemcpyAsync(X, sp.theta0, TN * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  EN_RC(tc_split(sp.K, NN, kh, kl, st));
   EN_RC(tc_encode_bf16_2d(&mAh, kh, N, N, tc::BM));
   EN_RC(tc_encode_bf16_2d(&mAl, kl, N, N, tc::BM));
   EN_RC(tc_encode_bf16_2d(&mBh, vh, 2 * T, N, BNT));
@@ -483,9 +514,10 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B2, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
   EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B3, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
   EN_CUDA(cudaFuncSetAttribute(ens_gemm_kernel<E_B4, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, PT::SMEM_BYTES));
+  std::memset(&a, 0, sizeof(a));
   a.N = (int)N;
   a.T = (int)T;
-  a.omega = omega;
+  a.omega = sp.omega;
   a.X = X;
   a.K14 = K14;
   a.K2 = K2;
@@ -500,97 +532,196 @@ int ensemble_solve_impl(const float* K, int64_t N, int64_t T, const double* omeg
   a.tr.status = isc + 5 * T; a.tr.any_live = isc + 6 * T;
   a.tr.n_acc = lsc; a.tr.n_rej = lsc + T; a.tr.n_rhs = lsc + 2 * T;
   a.tr.emax = usc; a.tr.red0 = usc + T; a.tr.red1 = usc + 2 * T; a.tr.red2 = usc + 3 * T;
-  a.rtol = rtol;
-  a.atol = atol;
-  a.t1 = t1;
-  a.hmax = 0.1 * (t1 - t0);
+  a.rtol = sp.rtol;
+  a.atol = sp.atol;
+  a.t1 = sp.t1;
+  a.hmax = 0.1 * (sp.t1 - sp.t0);
   a.hmin = 100.0 * DBL_EPSILON;
   a.max_attempts = 100000;
   a.max_rejects = 85000;
-  {
-    // t = t0 and every trajectory live
-    std::vector<double> tt(T, t0);
-    std::vector<int> ones(T, 1);
-    EN_CUDA(cudaMemcpyAsync(a.tr.t, tt.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
-    EN_CUDA(cudaMemcpyAsync(a.tr.live, ones.data(), T * sizeof(int), cudaMemcpyHostToDevice, st));
-    EN_CUDA(cudaStreamSynchronize(st));
-  }
-  // ---- K1 = f(t0, y0) and the starting step of every trajectory
-  // (j-vector operand copy 0 throughout; these epilogues write no j-vector)
-  a.Vh = (__nv_bfloat16*)vh;
-  a.Vl = (__nv_bfloat16*)vl;
-  ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 0);
-  a.phase = E_K1;
-  ens_gemm_kernel<E_K1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
-  ens_control<<<ctl_blocks, 256, 0, st>>>(a, 0);
-  ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 1);
-  a.phase = E_F1;
-  ens_gemm_kernel<E_F1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
-  ens_control<<<ctl_blocks, 256, 0, st>>>(a, 1);
+  // t = t0 and every trajectory live
+  std::vector<double> tt(T, sp.t0);
+  std::vector<int> ones(T, 1);
+  EN_CUDA(cudaMemcpyAsync(a.tr.t, tt.data(), T * sizeof(double), cudaMemcpyHostToDevice, st));
+  EN_CUDA(cudaMemcpyAsync(a.tr.live, ones.data(), T * sizeof(int), cudaMemcpyHostToDevice, st));
+  EN_CUDA(cudaStreamSynchronize(st));
+  return BS3_OK;
+}
+
+// The whole solve, recorded into the capture in progress on st:
+//   K1 = f(t0, y0) and the starting step (j-vector operand copy 0; these
+//   epilogues write no j-vector), then the attempt loop (WHILE node): the
+//   prologue (Y2 -> copy 0), stage 2 (reads copy 0, writes Y3 to copy 1),
+//   stage 3 (reads copy 1, writes X' to copy 0), stage 4 (reads copy 0), the
+//   per-trajectory control and the loop condition, all decided on the
+//   device; then the gather of the final phases.
+template <int BNT>
+int EnsembleRunT<BNT>::capture(cudaStream_t st, cudaStream_t body, cudaEvent_t loop_begin, cudaEvent_t loop_end) {
+  const long long spin = 1ll << 22;
+  EArgs b = a;
+  b.Vh = (__nv_bfloat16*)vh;
+  b.Vl = (__nv_bfloat16*)vl;
+  ens_prologue<<<ew_blocks, 256, 0, st>>>(b, 0);
+  b.phase = E_K1;
+  ens_gemm_kernel<E_K1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, b, (int)N, derr, spin);
+  ens_control<<<ctl_blocks, 256, 0, st>>>(b, 0);
+  ens_prologue<<<ew_blocks, 256, 0, st>>>(b, 1);
+  b.phase = E_F1;
+  ens_gemm_kernel<E_F1, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, b, (int)N, derr, spin);
+  EN_CUDA(cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st));
+  ens_control<<<ctl_blocks, 256, 0, st>>>(b, 1);
   EN_CUDA(cudaGetLastError());
-  // ---- U attempts per graph: prologue (Y2 -> copy 0), stage 2 (reads copy 0,
-  // writes Y3 to copy 1), stage 3 (reads copy 1, writes X' to copy 0), stage 4
-  // (reads copy 0), control
-  EN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  for (int u = 0; u < U; ++u) {
-    a.Vh = (__nv_bfloat16*)vh;
-    a.Vl = (__nv_bfloat16*)vl;
-    ens_prologue<<<ew_blocks, 256, 0, st>>>(a, 2);
-    a.phase = E_B2;
-    a.Vh = (__nv_bfloat16*)vh1;
-    a.Vl = (__nv_bfloat16*)vl1;
-    ens_gemm_kernel<E_B2, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
-    a.phase = E_B3;
-    a.Vh = (__nv_bfloat16*)vh;
-    a.Vl = (__nv_bfloat16*)vl;
-    ens_gemm_kernel<E_B3, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh1, mBl1, a, (int)N, derr, 1ll << 22);
-    a.phase = E_B4;
-    ens_gemm_kernel<E_B4, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, st>>>(mAh, mAl, mBh, mBl, a, (int)N, derr, 1ll << 22);
-    if (u == U - 1) cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), st);   // report the last attempt only
-    ens_control<<<ctl_blocks, 256, 0, st>>>(a, 2);
+  // the loop condition, set on the device before the loop and after each attempt
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  EN_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+  if (cs != cudaStreamCaptureStatusActive) return BS3_ERR_CUDA;
+  cudaGraphConditionalHandle h;
+  EN_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
+  ens_loop_start<<<1, 1, 0, st>>>(h, a.tr.any_live, derr, iters);
+  if (loop_begin) EN_CUDA(cudaEventRecord(loop_begin, st));
+  EN_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t loop;
+  EN_CUDA(cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp));
+  EN_CUDA(cudaStreamUpdateCaptureDependencies(st, &loop, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // the loop body, captured on the second stream into the node's body graph
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  EN_CUDA(cudaStreamBeginCaptureToGraph(body, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    const long long max_iters = max_lockstep > 0 ? max_lockstep : a.max_attempts + 1;
+    EArgs c = a;
+    c.Vh = (__nv_bfloat16*)vh;
+    c.Vl = (__nv_bfloat16*)vl;
+    ens_prologue<<<ew_blocks, 256, 0, body>>>(c, 2);
+    c.phase = E_B2;
+    c.Vh = (__nv_bfloat16*)vh1;
+    c.Vl = (__nv_bfloat16*)vl1;
+    ens_gemm_kernel<E_B2, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, body>>>(mAh, mAl, mBh, mBl, c, (int)N, derr, spin);
+    c.phase = E_B3;
+    c.Vh = (__nv_bfloat16*)vh;
+    c.Vl = (__nv_bfloat16*)vl;
+    ens_gemm_kernel<E_B3, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, body>>>(mAh, mAl, mBh1, mBl1, c, (int)N, derr, spin);
+    c.phase = E_B4;
+    ens_gemm_kernel<E_B4, BNT><<<ggrid, kEnsThreads, PT::SMEM_BYTES, body>>>(mAh, mAl, mBh, mBl, c, (int)N, derr, spin);
+    cudaMemsetAsync(a.tr.any_live, 0, sizeof(int), body);
+    ens_control<<<ctl_blocks, 256, 0, body>>>(c, 2);
+    ens_loop_next<<<1, 1, 0, body>>>(h, a.tr.any_live, derr, iters, max_iters);
   }
-  EN_CUDA(cudaStreamEndCapture(st, &graph));
-  EN_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-  if (loop_ms) {
-    EN_CUDA(cudaEventCreate(&ev0));
-    EN_CUDA(cudaEventCreate(&ev1));
-    EN_CUDA(cudaEventRecord(ev0, st));
-  }
-  while (any) {
-    EN_CUDA(cudaGraphLaunch(exec, st));
-    EN_CUDA(cudaMemcpyAsync(&any, a.tr.any_live, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EN_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EN_CUDA(cudaStreamSynchronize(st));
-    iters += U;
-    if (herr) { rc = BS3_ERR_DEVICE_WAIT; break; }
-    if (iters > a.max_attempts + U) break;
-    if (max_lockstep > 0 && iters >= max_lockstep && any) { rc = BS3_ERR_MAX_STEPS; break; }
-  }
-  if (loop_ms) {
-    EN_CUDA(cudaEventRecord(ev1, st));
-    EN_CUDA(cudaEventSynchronize(ev1));
-    EN_CUDA(cudaEventElapsedTime(loop_ms, ev0, ev1));
-  }
+  const cudaError_t eb = cudaGetLastError();
+  cudaGraph_t ended = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(body, &ended);
+  if (eb != cudaSuccess || ee != cudaSuccess) return BS3_ERR_CUDA;
+  if (loop_end) EN_CUDA(cudaEventRecord(loop_end, st));
   ens_gather<<<ew_blocks, 256, 0, st>>>(a, theta_out);
   EN_CUDA(cudaGetLastError());
-  EN_CUDA(cudaStreamSynchronize(st));
-  if (n_acc) EN_CUDA(cudaMemcpy(n_acc, a.tr.n_acc, T * sizeof(long long), cudaMemcpyDeviceToHost));
-  if (n_rej) EN_CUDA(cudaMemcpy(n_rej, a.tr.n_rej, T * sizeof(long long), cudaMemcpyDeviceToHost));
-  if (status) EN_CUDA(cudaMemcpy(status, a.tr.status, T * sizeof(int), cudaMemcpyDeviceToHost));
-  if (lockstep_attempts) *lockstep_attempts = iters;
-done:
-  if (own) {
-    cudaStreamSynchronize(own);
-    cudaStreamDestroy(own);
+  return BS3_OK;
+}
+
+template <int BNT>
+int EnsembleRunT<BNT>::finish(int64_t* n_acc, int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts) {
+  int herr = 0, any = 0;
+  long long it = 0;
+  EN_CUDA(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EN_CUDA(cudaMemcpyAsync(&any, a.tr.any_live, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EN_CUDA(cudaMemcpyAsync(&it, iters, sizeof(long long), cudaMemcpyDeviceToHost, stream));
+  if (n_acc) EN_CUDA(cudaMemcpyAsync(n_acc, a.tr.n_acc, T * sizeof(long long), cudaMemcpyDeviceToHost, stream));
+  if (n_rej) EN_CUDA(cudaMemcpyAsync(n_rej, a.tr.n_rej, T * sizeof(long long), cudaMemcpyDeviceToHost, stream));
+  if (status) EN_CUDA(cudaMemcpyAsync(status, a.tr.status, T * sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EN_CUDA(cudaStreamSynchronize(stream));
+  if (lockstep_attempts) *lockstep_attempts = it;
+  if (herr) return BS3_ERR_DEVICE_WAIT;
+  if (any && max_lockstep > 0 && it >= max_lockstep) return BS3_ERR_MAX_STEPS;
+  return BS3_OK;
+}
+
+#undef EN_CUDA
+#undef EN_RC
+
+template <int BNT>
+int create_t(const EnsembleSpec& sp, cudaStream_t st, EnsembleRun** out) {
+  auto* r = new EnsembleRunT<BNT>();
+  const int rc = r->init(sp, st);
+  if (rc != BS3_OK) {
+    delete r;
+    return rc;
   }
+  *out = r;
+  return BS3_OK;
+}
+
+}  // namespace
+
+int ensemble_create(const EnsembleSpec& sp, cudaStream_t st, EnsembleRun** out) {
+  if (!out) return BS3_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int tile = sp.tile_n == 0 ? 128 : sp.tile_n;
+  if (!sp.K || !sp.omega || !sp.theta0 || !sp.theta_out || (tile != 128 && tile != 256)) return BS3_ERR_INVALID_ARG;
+  if (sp.N < tc::BM || sp.N % tc::BM || sp.N % tc::BK || sp.T < tile / 2 || (2 * sp.T) % tile) return BS3_ERR_INVALID_ARG;
+  if (sp.N > (1 << 20) || sp.T > (1 << 16) || sp.max_lockstep < 0 || sp.max_ctas < 0) return BS3_ERR_INVALID_ARG;
+  if (!(sp.t1 > sp.t0) || !(sp.rtol > 0.0) || !(sp.atol >= 0.0)) return BS3_ERR_INVALID_ARG;
+  return tile == 256 ? create_t<256>(sp, st, out) : create_t<128>(sp, st, out);
+}
+
+}  // namespace bs3
+
+using namespace bs3;
+using namespace bs3::ens;
+
+namespace {
+
+// A standalone ensemble solve: one graph (set-up stages, the attempt loop as a
+// device-decided WHILE node, the gather), launched once; the host waits only
+// for its end.  loop_ms (optional) receives the device time of the attempt
+// loop alone.
+int ensemble_solve_graph(const EnsembleSpec& sp, int64_t* n_acc, int64_t* n_rej, int32_t* status,
+                         int64_t* lockstep_attempts, cudaStream_t st_in, float* loop_ms) {
+  cudaStream_t st = st_in, own = nullptr, body = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  EnsembleRun* run = nullptr;
+  int rc = BS3_OK;
+  do {
+    if (st == nullptr) {   // graphs cannot be captured on the legacy default stream
+      if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaDeviceSynchronize() != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+      st = own;
+    }
+    if (cudaStreamCreateWithFlags(&body, cudaStreamNonBlocking) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    if (loop_ms && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess)) {
+      rc = BS3_ERR_CUDA;
+      break;
+    }
+    rc = ensemble_create(sp, st, &run);
+    if (rc != BS3_OK) break;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    rc = run->capture(st, body, ev0, ev1);
+    const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+    if (rc != BS3_OK) break;
+    if (ee != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess ||
+        cudaGraphLaunch(exec, st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+    rc = run->finish(n_acc, n_rej, status, lockstep_attempts);
+    if (loop_ms && cudaEventElapsedTime(loop_ms, ev0, ev1) != cudaSuccess && rc == BS3_OK) rc = BS3_ERR_CUDA;
+  } while (0);
+  if (own) cudaStreamSynchronize(own);
+  if (st_in) cudaStreamSynchronize(st_in);
+  delete run;
   if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  if (graph) cudaGraphDestroy(graph);
-  cudaFree(kh); cudaFree(kl); cudaFree(vh); cudaFree(vl); cudaFree(vh1); cudaFree(vl1); cudaFree(scb); cudaFree(scx); cudaFree(X); cudaFree(K14); cudaFree(K2); cudaFree(E3);
-  cudaFree(dsc); cudaFree(isc); cudaFree(lsc); cudaFree(usc); cudaFree(derr);
+  if (body) cudaStreamDestroy(body);
+  if (own) cudaStreamDestroy(own);
   return rc;
 }
+
+}  // namespace
 
 extern "C" int bs3_ensemble_solve_tiled(const float* K, int64_t N, int64_t T, const double* omega,
                                         const double* theta0, double t0, double t1, double rtol, double atol,
@@ -598,14 +729,9 @@ extern "C" int bs3_ensemble_solve_tiled(const float* K, int64_t N, int64_t T, co
                                         int64_t* n_rej, int32_t* status, int64_t* lockstep_attempts, void* stream) {
   // narrow tiles by default: more tiles per persistent CTA, so more of each
   // binary64 epilogue overlaps the next tile's products
-  if (tile_n == 0) tile_n = 128;
-  if (tile_n == 256)
-    return ensemble_solve_impl<256>(K, N, T, omega, theta0, t0, t1, rtol, atol, max_lockstep, theta_out, n_acc,
-                                    n_rej, status, lockstep_attempts, stream);
-  if (tile_n == 128)
-    return ensemble_solve_impl<128>(K, N, T, omega, theta0, t0, t1, rtol, atol, max_lockstep, theta_out, n_acc,
-                                    n_rej, status, lockstep_attempts, stream);
-  return BS3_ERR_INVALID_ARG;
+  const EnsembleSpec sp{K, N, T, omega, theta0, t0, t1, rtol, atol, tile_n == 0 ? 128 : tile_n, max_lockstep, 0,
+                        theta_out};
+  return ensemble_solve_graph(sp, n_acc, n_rej, status, lockstep_attempts, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int bs3_ensemble_solve(const float* K, int64_t N, int64_t T, const double* omega, const double* theta0,
@@ -629,11 +755,8 @@ extern "C" int bs3_ensemble_autotune(const float* K, int64_t N, int64_t T, const
     for (int rep = 0; rep < 2; ++rep) {
       int64_t steps = 0;
       float ms = 0.f;
-      const int r = tile == 256
-                        ? ensemble_solve_impl<256>(K, N, T, omega, theta0, t0, t1, rtol, atol, lockstep_attempts,
-                                                   scratch_theta, nullptr, nullptr, nullptr, &steps, nullptr, &ms)
-                        : ensemble_solve_impl<128>(K, N, T, omega, theta0, t0, t1, rtol, atol, lockstep_attempts,
-                                                   scratch_theta, nullptr, nullptr, nullptr, &steps, nullptr, &ms);
+      const EnsembleSpec sp{K, N, T, omega, theta0, t0, t1, rtol, atol, tile, lockstep_attempts, 0, scratch_theta};
+      const int r = ensemble_solve_graph(sp, nullptr, nullptr, nullptr, &steps, nullptr, &ms);
       if (r != BS3_OK && r != BS3_ERR_MAX_STEPS) return r;
       us = 1e3 * ms / (double)std::max<int64_t>(1, steps);
     }

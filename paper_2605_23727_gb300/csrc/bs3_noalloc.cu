@@ -65,10 +65,13 @@ int scratch_address(int device, unsigned char** out) {
 // Per-call set-up of the scratch: row scales (1), row sums of the weights
 // (paper-form oscillators), k1/(k0-k1) (circadian) and zeroed j-vectors (their
 // padding columns multiply zero weights and must not hold stale NaN or Inf).
+// A circadian k1_i outside (0, k0) sets the control block's status to
+// S_INVALID (the check bs3_create_system makes on the host).
 template <typename W>
 __global__ void noalloc_setup(const W* __restrict__ w, int64_t N, int64_t ld, const double* __restrict__ par,
                               int kind, double k0, float* __restrict__ scale, double* __restrict__ rowsum,
-                              double* __restrict__ theta, float* __restrict__ jv32, double* __restrict__ jv64) {
+                              double* __restrict__ theta, float* __restrict__ jv32, double* __restrict__ jv64,
+                              Control* __restrict__ ctrl) {
   const int64_t i = blockIdx.x;
   double acc = 0.0;
   if (kind == BS3_LCO_PAPER)
@@ -84,6 +87,7 @@ __global__ void noalloc_setup(const W* __restrict__ w, int64_t N, int64_t ld, co
     rowsum[i] = r;
     scale[i] = 1.0f;
     theta[i] = (kind == BS3_CIRCADIAN) ? par[i] / (k0 - par[i]) : 0.0;
+    if (kind == BS3_CIRCADIAN && !(par[i] > 0.0 && par[i] < k0)) atomicCAS(&ctrl->status, 0, (int)S_INVALID);
   }
   for (int64_t e = i * blockDim.x + threadIdx.x; e < 6 * ld; e += (int64_t)gridDim.x * blockDim.x) {
     jv32[e] = 0.0f;
@@ -91,9 +95,13 @@ __global__ void noalloc_setup(const W* __restrict__ w, int64_t N, int64_t ld, co
   }
 }
 
+// A failed CUDA call ends the entry point with BS3_ERR_CUDA, also in the stats.
 #define NA_CUDA(call)                           \
   do {                                          \
-    if ((call) != cudaSuccess) return BS3_ERR_CUDA; \
+    if ((call) != cudaSuccess) {                \
+      if (stats) stats->status = BS3_ERR_CUDA;  \
+      return BS3_ERR_CUDA;                      \
+    }                                           \
   } while (0)
 
 }  // namespace
@@ -109,18 +117,25 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   }
   if (kind < BS3_LCO_CFG || kind > BS3_CIRCADIAN) return BS3_ERR_INVALID_ARG;
   if (N < 1 || N > kNoAllocMaxN) return BS3_ERR_INVALID_ARG;   // beyond the static scratch
-  if (ld < N || ld % 16 != 0 || (store != BS3_F64 && store != BS3_F32) || !weights || !y0) return BS3_ERR_INVALID_ARG;
+  // the j-vector regions of the scratch hold kLdMax columns
+  if (ld < N || ld > kLdMax || ld % 16 != 0 || (store != BS3_F64 && store != BS3_F32) || !weights || !y0)
+    return BS3_ERR_INVALID_ARG;
   if (((uintptr_t)weights & 15) != 0) return BS3_ERR_INVALID_ARG;
   if ((kind != BS3_LCO_PAPER && !par) || (kind == BS3_CIRCADIAN && !globals)) return BS3_ERR_INVALID_ARG;
+  if (kind == BS3_CIRCADIAN && !(std::isfinite(globals[0]) && globals[0] > 0.0)) return BS3_ERR_INVALID_ARG;
   if (!(t1 > t0) || !std::isfinite(t0) || !std::isfinite(t1) || !(rtol > 0.0) || !(atol >= 0.0)) return BS3_ERR_INVALID_ARG;
   if (variant < BS3_SINGLE || variant > BS3_DOUBLE || accum < BS3_ACC_F32 || accum > BS3_ACC_F64) return BS3_ERR_INVALID_ARG;
   if (n_out < 0 || (n_out > 0 && (!t_out || !y_out))) return BS3_ERR_INVALID_ARG;
+  if (stats) stats->status = BS3_OK;   // the arguments are valid; later failures are CUDA errors
   cudaStream_t stream = (cudaStream_t)stream_;
   int device = 0;
   NA_CUDA(cudaGetDevice(&device));
   unsigned char* base = nullptr;
   int rc = scratch_address(device, &base);
-  if (rc != BS3_OK) return rc;
+  if (rc != BS3_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
   Control* ctrl = (Control*)(base + kOffCtrl);
   float* jv32 = (float*)(base + kOffJv32);
   double* jv64 = (double*)(base + kOffJv64);
@@ -132,14 +147,24 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   // paper-form oscillators have no per-agent parameter: any readable array will do
   const double* par_k = par ? par : rowsum;
 
+  NA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Control), stream));
   if (store == BS3_F64)
     noalloc_setup<double><<<(unsigned)N, 128, 0, stream>>>((const double*)weights, N, ld, par_k, kind, k0, scale,
-                                                           rowsum, theta, jv32, jv64);
+                                                           rowsum, theta, jv32, jv64, ctrl);
   else
     noalloc_setup<float><<<(unsigned)N, 128, 0, stream>>>((const float*)weights, N, ld, par_k, kind, k0, scale,
-                                                          rowsum, theta, jv32, jv64);
+                                                          rowsum, theta, jv32, jv64, ctrl);
   NA_CUDA(cudaGetLastError());
-  NA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Control), stream));
+  if (kind == BS3_CIRCADIAN) {
+    // the per-cell check of k1 ran on the device: read its verdict first
+    int bad = 0;
+    NA_CUDA(cudaMemcpyAsync(&bad, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    NA_CUDA(cudaStreamSynchronize(stream));
+    if (bad != 0) {
+      if (stats) stats->status = BS3_ERR_INVALID_ARG;
+      return BS3_ERR_INVALID_ARG;
+    }
+  }
 
   // launch plan as for a system: one CTA per SM, weights kept in shared memory
   // when the rows of every CTA fit
@@ -153,7 +178,7 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   const size_t slab = ((size_t)rcap * ld * (store == BS3_F64 ? 8 : 4) + 127) / 128 * 128;
   const bool resident = kind != BS3_CIRCADIAN && slab + state <= (size_t)224 * 1024;
   const size_t smem = (resident ? slab : 0) + state;
-  NA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NA_CUDA(allow_max_smem(kern, device));
 
   Args a;
   std::memset(&a, 0, sizeof(a));

@@ -1292,6 +1292,7 @@ struct SysDesc {
   double* jv64;      // [3][2][ld]
   Control* ctrl;
   double t0, t1;
+  double rtol, atol;   // this system's tolerances (Rel, Ab of Eq. ERROR-O23)
 };
 
 struct BatchArgs {
@@ -1331,6 +1332,8 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   a.final_y = D.y_final;
   a.t0 = D.t0;
   a.t1 = D.t1;
+  a.rtol = D.rtol;
+  a.atol = D.atol;
   a.hmax = 0.1 * (D.t1 - D.t0);
   a.n_out = 0;
   a.slab_bytes = 0;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -30,6 +31,20 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                    long long ldc, int K, int* err, long long spin) {
   const tc::StoreRowMajor st{C, ldc};
   tc::gemm_tile<4, tc::BN>(&mAh, &mAl, &mBh, &mBl, blockIdx.x * tc::BM, blockIdx.y * tc::BN, K, st, err, spin);
+}
+
+// The product as the ensembles' stage products run it: persistent CTAs with
+// two tensor-memory accumulators and 16 epilogue warps (gemm_persistent), the
+// epilogue storing the binary32 accumulators row-major.
+constexpr int kPersistEpiWarps = 16;
+
+template <int BNT>
+__global__ void __launch_bounds__(tc::threads_for(kPersistEpiWarps), 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                              float* C, long long ldc, int tiles_m, int tiles_n, int K, int* err, long long spin) {
+  const tc::StoreRowMajor st{C, ldc};
+  tc::gemm_persistent<kPersistEpiWarps, BNT>(&mAh, &mAl, &mBh, &mBl, tiles_m, tiles_n, K, st, err, spin);
 }
 
 namespace {
@@ -109,4 +124,54 @@ extern "C" int bs3_tc_gemm(int64_t M, int64_t Nc, int64_t K, const float* A, con
 done:
   cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(derr);
   return rc;
+}
+
+template <int BNT>
+static int tc_gemm_persistent_impl(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C,
+                                   int max_ctas) {
+  using PT = tc::PTile<BNT>;
+  int rc = BS3_OK;
+  void *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* derr = nullptr;
+  int herr = 0, dev = 0, sms = 0;
+  int64_t tiles = 0;
+  unsigned grid = 0;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  TC_CUDA(cudaGetDevice(&dev));
+  TC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  tiles = (M / tc::BM) * (Nc / BNT);
+  grid = (unsigned)std::min<int64_t>(tiles, max_ctas > 0 ? std::min(max_ctas, sms) : sms);
+  TC_CUDA(cudaMalloc(&ah, M * K * 2));
+  TC_CUDA(cudaMalloc(&al, M * K * 2));
+  TC_CUDA(cudaMalloc(&bh, Nc * K * 2));
+  TC_CUDA(cudaMalloc(&bl, Nc * K * 2));
+  TC_CUDA(cudaMalloc(&derr, sizeof(int)));
+  TC_CUDA(cudaMemset(derr, 0, sizeof(int)));
+  TC_RC(tc_split(A, (size_t)(M * K), ah, al, 0));
+  TC_RC(tc_split(B, (size_t)(Nc * K), bh, bl, 0));
+  TC_RC(tc_encode_bf16_2d(&mAh, ah, M, K, tc::BM));
+  TC_RC(tc_encode_bf16_2d(&mAl, al, M, K, tc::BM));
+  TC_RC(tc_encode_bf16_2d(&mBh, bh, Nc, K, BNT));
+  TC_RC(tc_encode_bf16_2d(&mBl, bl, Nc, K, BNT));
+  TC_CUDA(cudaFuncSetAttribute(tc_gemm_persistent_kernel<BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               PT::SMEM_BYTES));
+  tc_gemm_persistent_kernel<BNT><<<grid, tc::threads_for(kPersistEpiWarps), PT::SMEM_BYTES>>>(
+      mAh, mAl, mBh, mBl, C, (long long)Nc, (int)(M / tc::BM), (int)(Nc / BNT), (int)K, derr, (long long)1 << 22);
+  TC_CUDA(cudaGetLastError());
+  TC_CUDA(cudaDeviceSynchronize());
+  TC_CUDA(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr) rc = BS3_ERR_DEVICE_WAIT;
+done:
+  cudaFree(ah); cudaFree(al); cudaFree(bh); cudaFree(bl); cudaFree(derr);
+  return rc;
+}
+
+extern "C" int bs3_tc_gemm_persistent(int64_t M, int64_t Nc, int64_t K, const float* A, const float* B, float* C,
+                                      int tile_n, int max_ctas) {
+  if (tile_n != 128 && tile_n != 256) return BS3_ERR_INVALID_ARG;
+  if (M < tc::BM || Nc < tile_n || K < tc::BK || M % tc::BM || Nc % tile_n || K % tc::BK || !A || !B || !C)
+    return BS3_ERR_INVALID_ARG;
+  if (K > (1 << 30) || M > (1 << 30) || Nc > (1 << 30) || max_ctas < 0) return BS3_ERR_INVALID_ARG;
+  return tile_n == 128 ? tc_gemm_persistent_impl<128>(M, Nc, K, A, B, C, max_ctas)
+                       : tc_gemm_persistent_impl<256>(M, Nc, K, A, B, C, max_ctas);
 }

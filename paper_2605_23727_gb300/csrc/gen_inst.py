@@ -21,6 +21,7 @@ for kname, kenum in KINDS:
 
 with open(os.path.join(HERE, "bs3_kernels.h"), "w") as fh:
     fh.write("// Generated by gen_inst.py: kernel lookup across translation units.\n#pragma once\n\n"
+             "#include <cuda_runtime.h>\n\n"
              "namespace bs3 {\n")
     for kname, _ in KINDS:
         for sname, _ in STORES:
@@ -35,4 +36,20 @@ with open(os.path.join(HERE, "bs3_kernels.h"), "w") as fh:
              "  static const void* (*const table[4][5])() = {\n")
     for kname, _ in KINDS:
         fh.write("      {" + ", ".join(f"batch_kernel_{kname}_{s}" for s, _ in STORES) + "},\n")
-    fh.write("  };\n  return table[kind][store]();\n}\n}  // namespace bs3\n")
+    fh.write("  };\n  return table[kind][store]();\n}\n\n")
+    fh.write("// Sets a kernel's dynamic shared-memory limit to the largest value the\n"
+             "// device allows.  The limit is an attribute of the kernel, shared by every\n"
+             "// caller in the process, so it only ever takes this one value: a smaller\n"
+             "// value set for one launch would make another launch of the same kernel\n"
+             "// with more shared memory fail.\n"
+             "inline cudaError_t allow_max_smem(const void* kern, int device) {\n"
+             "  int optin = 0;\n"
+             "  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);\n"
+             "  if (e != cudaSuccess) return e;\n"
+             "  cudaFuncAttributes fa;\n"
+             "  e = cudaFuncGetAttributes(&fa, kern);\n"
+             "  if (e != cudaSuccess) return e;\n"
+             "  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,\n"
+             "                              optin - (int)fa.sharedSizeBytes);\n"
+             "}\n"
+             "}  // namespace bs3\n")

@@ -137,3 +137,102 @@ def test_ragged_1000_sampled_systems_match_single_solves():
         n_b = stats[k].n_accepted + stats[k].n_rejected
         assert abs((st.n_accepted + st.n_rejected) - n_b) <= 2, (k, w.N)
         np.testing.assert_allclose(yf[offs[k]:offs[k + 1]], y, rtol=0, atol=1e-6)
+
+
+def test_ensemble_256x8192_sampled_trajectories_against_oracle():
+    """Three trajectories of the coupled full-size ensemble (T = 256, N = 8192,
+    t in [0, 0.5], rtol 1e-6) against the oracle's tensor variant solved one by
+    one: attempt counts within 5 %, final phases within a bound derived from
+    the one place the two differ.  Both use the same bfloat16 split of K and of
+    the sine/cosine; the oracle sums the three split products exactly and
+    rounds once, the tensor cores round every accumulation toward zero.  With
+    3N/16 accumulations of at most one binary32 ulp of a running sum bounded by
+    R_i = sum_j |K_ij| (|sin|, |cos| <= 1), a coupling differs by at most
+    d = 2 (3N/16) 2^-23 max_i R_i; over the span, by Gronwall with the
+    Lipschitz constant L = 2 max_i R_i, the phases by d (e^{L t} - 1) / L.  A
+    wrong stage combination, a stale operand copy or a sign error in the
+    epilogue exceeds it; the split itself and the tiling are pinned exactly by
+    the one-hot products of tests/test_gpu_tc.py."""
+    bs3 = library()
+    torch = torch_cuda()
+    from oracle import bs3 as obs3
+    T, N, t1, rtol = 256, 8192, 0.5, 1e-6
+    K, omega, theta0 = W.kuramoto_ensemble(T=T, N=N, seed=14)
+    Kd = torch.tensor(K, dtype=torch.float32, device="cuda")
+    om = torch.tensor(omega, device="cuda")
+    th = torch.tensor(theta0, device="cuda")
+    out = torch.empty_like(th)
+    rc, n_acc, n_rej, status, _ = bs3.bs3_ensemble_solve(Kd, N, T, om, th, 0.0, t1, rtol, rtol, out)
+    assert rc == bs3.OK and np.all(status == 0)
+    del Kd
+    y = out.cpu().numpy()
+    R = float(np.max(np.abs(K.astype(np.float64)).sum(axis=1)))
+    d = 2.0 * (3 * N / 16) * 2.0 ** -23 * R
+    L = 2.0 * R
+    bound = d * (np.exp(L * t1) - 1.0) / L
+    osys = models.make_system("kuramoto", N, omega[0], K, "f32")
+    for b in (0, 127, 255):
+        osys.params = np.asarray(omega[b], dtype=np.float64)
+        ref = obs3.solve(osys, 0.0, t1, theta0[b], rtol, rtol, "tensor")
+        assert ref.status == obs3.OK
+        n_gpu, n_ref = int(n_acc[b] + n_rej[b]), ref.n_accepted + ref.n_rejected
+        assert abs(n_gpu - n_ref) <= max(2, 0.05 * n_ref), (b, n_gpu, n_ref)
+        dev = float(np.max(np.abs(y[b] - ref.y)))
+        print(f"trajectory {b}: attempts gpu {n_gpu} oracle {n_ref}, max |dtheta| {dev:.3e} (bound {bound:.3e})")
+        assert dev <= bound, (b, dev, bound)
+
+
+def test_config4_group_and_1000_systems_in_one_submission():
+    """The shared-K batch configuration in one bs3_solve_batch call: 256
+    Kuramoto trajectories at N = 8192 sharing K (t in [0, 0.5]) beside 1000
+    second-order oscillator systems with N log-uniform in [64, 4096] (binary16
+    weights, Mixed1, t in [0, 10]).  The group equals the standalone ensemble
+    entry's solve (same products and decisions); the four smallest systems
+    match their oracle solves; the largest (solved by a team of CTAs) matches
+    its standalone bs3_solve."""
+    bs3 = library()
+    torch = torch_cuda()
+    from oracle import bs3 as obs3
+    from oracle import metrics
+    systems = W.lco_ragged_batch(count=1000, n_min=64, n_max=4096, seed=0, t1=10.0, rtol=1e-6)
+    handles, items, outs = [], [], []
+    for w in systems:
+        s = bs3.System.from_workload(w, "f16")
+        handles.append(s)
+        y0 = torch.tensor(w.y0, device="cuda")
+        yf = torch.full_like(y0, float("nan"))
+        outs.append(yf)
+        items.append({"sys": s.handle, "y0": y0, "y_final": yf, "t0": w.t0, "t1": w.t1, "rtol": 1e-6, "atol": 1e-6})
+    T, N, t1 = 256, 8192, 0.5
+    K, omega, theta0 = W.kuramoto_ensemble(T=T, N=N, seed=15)
+    g = {"K": torch.tensor(K, device="cuda"), "N": N, "T": T, "omega": torch.tensor(omega, device="cuda"),
+         "theta0": torch.tensor(theta0, device="cuda"), "t0": 0.0, "t1": t1, "rtol": 1e-6, "atol": 1e-6,
+         "n_acc": np.zeros(T, dtype=np.int64), "n_rej": np.zeros(T, dtype=np.int64),
+         "status": np.zeros(T, dtype=np.int32)}
+    g["theta_out"] = torch.full_like(g["theta0"], float("nan"))
+    rc, stats, steps, ms = bs3.bs3_solve_batch(items, bs3.MIXED1, bs3.ACC_FLOAT2, 0, g)
+    assert rc == bs3.OK, bs3.bs3_status_string(rc)
+    assert all(st.status == 0 and st.t_reached == 10.0 for st in stats)
+    assert np.all(g["status"] == 0)
+    out = torch.empty_like(g["theta0"])
+    rc, n_acc, n_rej, status, steps2 = bs3.bs3_ensemble_solve(g["K"], N, T, g["omega"], g["theta0"], 0.0, t1, 1e-6,
+                                                              1e-6, out)
+    assert rc == bs3.OK and steps == steps2 and np.array_equal(n_acc, g["n_acc"])
+    np.testing.assert_array_equal(out.cpu().numpy(), g["theta_out"].cpu().numpy())
+    del out, g
+    order = np.argsort([w.N for w in systems])
+    for k in order[:4]:
+        w = systems[k]
+        ref = obs3.solve(models.from_workload(w, "f16"), w.t0, w.t1, w.y0, 1e-6, 1e-6, "mixed1")
+        n_gpu, n_ref = stats[k].n_accepted + stats[k].n_rejected, ref.n_accepted + ref.n_rejected
+        assert abs(n_gpu - n_ref) <= max(2, 0.05 * n_ref), (k, w.N, n_gpu, n_ref)
+        assert metrics.normalized_final_error(ref.y, outs[k].cpu().numpy(), w.N) < 1e-5, (k, w.N)
+    k = int(order[-1])
+    w = systems[k]
+    rc, st, y, _ = handles[k].solve(w.t0, w.t1, w.y0, 1e-6, 1e-6, "mixed1", "float2")
+    assert rc == bs3.OK
+    n_gpu, n_ref = stats[k].n_accepted + stats[k].n_rejected, st.n_accepted + st.n_rejected
+    assert abs(n_gpu - n_ref) <= max(2, 0.05 * n_ref)
+    assert metrics.normalized_final_error(y, outs[k].cpu().numpy(), w.N) < 1e-5
+    for h in handles:
+        h.close()
