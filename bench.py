@@ -79,6 +79,7 @@ CASES = {
     "phases_kuramoto4096_mixed1_f32": None,
     "sweep_kuramoto4096": None,
     "beta_gamma_suite": None,
+    "size_vs_error": None,
 }
 
 # FP32 instructions per pair of the circadian coupling (own arctangent): the
@@ -184,7 +185,10 @@ def run_batch_config4_case(name):
          "status": np.zeros(T, dtype=np.int32)}
     g["theta_out"] = torch.empty_like(g["theta0"])
     out = {"case": name}
-    for tag, its, grp in (("items_alone", items, None), ("group_alone", [], g), ("one_call", items, g)):
+    for tag, its, grp, ctas in (("items_alone", items, None, 0), ("group_alone", [], g, 0),
+                                ("one_call", items, g, 0), ("one_call_side_by_side_48", items, g, 48)):
+        if grp is not None:
+            grp["ctas"] = ctas
         for _ in range(2):          # the first call pays the one-time set-up
             rc, stats, steps, ms = bs3.bs3_solve_batch(its, bs3.MIXED1, bs3.ACC_FLOAT2, 0, grp)
         rec = {"status": bs3.bs3_status_string(rc), "ms": round(ms, 2)}
@@ -316,15 +320,15 @@ def run_beta_case(name):
                       "summary": summary}))
 
 
-def run_proposer_case(name):
-    """Second-order oscillators N = 32768, f16 weights, Mixed1, rtol 1e-6,
-    t in [0, 10], with and without the learned step-size proposer (trained on
-    step histories of the three smaller workloads, other seeds)."""
+def proposer_comparison(N=32768):
+    """Second-order oscillators (f16 weights, Mixed1, t in [0, 10]) with and
+    without the learned step-size proposer, trained on the GPU on step
+    histories of the three smaller workloads (other seeds).  Both at rtol 1e-6;
+    the proposer also at 5e-7, so that its time at the plain controller's
+    global error is interpolated (log-log) along its own curve.  Global errors
+    against a tight solve with the same weights (Mixed2, rtol 1e-9)."""
     import torch
     from paper_2605_23727_gb300 import bs3, proposer
-    import __graft_entry__
-    __graft_entry__.build()
-    bs3.load()
     train = []
     for seed in (101, 102, 103):
         for rtol in (1e-4, 1e-5, 1e-6, 1e-7):
@@ -333,7 +337,6 @@ def run_proposer_case(name):
     train.append((workloads.circadian(256, 101, t1=240.0), "f32", "mixed2", 1e-6))
     X, y = proposer.dataset(train)
     model, loss = proposer.train(X, y, epochs=120, batch=256, lr=2e-3)
-    N = 32768 if name == "proposer_lco32768_f16" else 8192
     w = workloads.lco_config(N, 7, t1=10.0, dtype=np.float32)
     s = bs3.System.from_workload(w, "f16")
     y0 = torch.tensor(w.y0, device="cuda")
@@ -347,20 +350,93 @@ def run_proposer_case(name):
                                None, 0, None, yo, 0)
         e1.record()
         e1.synchronize()
-        assert rc == bs3.OK, bs3.bs3_status_string(rc)
+        if rc != bs3.OK:
+            raise RuntimeError(bs3.bs3_status_string(rc))
         return yo.cpu().numpy(), st, e0.elapsed_time(e1)
 
     y_ref, _, _ = run(1e-9, "mixed2")     # same f16 weights, tight tolerance
+    run(RTOL, "mixed1")
     y_plain, st_plain, ms_plain = run(RTOL, "mixed1")
-    assert bs3.bs3_set_proposer(s.handle, model) == bs3.OK
+    if bs3.bs3_set_proposer(s.handle, model) != bs3.OK:
+        raise RuntimeError("bs3_set_proposer")
     run(RTOL, "mixed1")
     y_learn, st_learn, ms_learn = run(RTOL, "mixed1")
+    y_learn2, st_learn2, ms_learn2 = run(5e-7, "mixed1")
     s.close()
-    out = {"case": name, "N": N, "training_samples": int(len(y)), "final_train_loss": float(loss[-1])}
-    for tag, yv, st, ms in (("plain", y_plain, st_plain, ms_plain), ("learned", y_learn, st_learn, ms_learn)):
-        out[tag] = {"accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals, "ms": ms,
-                    "global_error_vs_tight": normalized_error(y_ref, yv, N)}
-    print(json.dumps(out))
+    out = {"workload": f"lco_cfg_N{N}_f16_mixed1_t10", "training_samples": int(len(y)),
+           "final_train_loss": float(loss[-1])}
+    for tag, yv, st, ms, rt in (("plain", y_plain, st_plain, ms_plain, RTOL),
+                                ("learned", y_learn, st_learn, ms_learn, RTOL),
+                                ("learned_rtol5e-7", y_learn2, st_learn2, ms_learn2, 5e-7)):
+        out[tag] = {"rtol": rt, "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": st.n_rhs_evals,
+                    "ms": round(ms, 3), "global_error_vs_tight": normalized_error(y_ref, yv, N)}
+    e_plain = out["plain"]["global_error_vs_tight"]
+    t_match = time_at([(out["learned"]["global_error_vs_tight"], ms_learn),
+                       (out["learned_rtol5e-7"]["global_error_vs_tight"], ms_learn2)], e_plain)
+    out["learned_ms_at_plain_error"] = None if t_match is None else round(t_match, 3)
+    out["speedup_at_matched_error"] = None if t_match is None else round(ms_plain / t_match, 4)
+    return out
+
+
+def run_size_case(name):
+    """Normalized final error against system size at fixed tolerance (Sec. 3.3,
+    Fig. Size-VS-Error) on the seeded synthetic benchmarks: Benchmark 1 (paper
+    form, heterogeneous M, t in [0, 10 pi]), Kuramoto (t in [0, 10]) and the
+    circadian model (t in [0, 48]), N in {256, 1024, 4096}, rtol = atol in
+    {1e-3, 1e-6, 1e-8}, seeds 0..2, the four solvers (binary32 weights, Double
+    binary64).  The reference is the GPU's binary64 solve at rtol = atol =
+    1e-11 of the same system (CPU DOPRI5 at these sizes takes hours; the
+    GPU Double path is validated against the oracle by the parity tests).
+    Per (benchmark, N, rtol, solver): the errors' (min, median, max)."""
+    import torch
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    makers = {
+        "LCO": lambda N, seed: workloads.lco_paper(N, seed, heterogeneous=True),
+        "Kur": lambda N, seed: workloads.kuramoto(N, seed, t1=10.0),
+        "CC": lambda N, seed: workloads.circadian(N, seed, t1=48.0),
+    }
+    solvers = (("single", "f32"), ("mixed1", "f32"), ("mixed2", "f32"), ("double", "f64"))
+    rows = []
+    for bench_name, make in makers.items():
+        for N in (256, 1024, 4096):
+            errs = {}
+            for seed in range(3):
+                w = make(N, seed)
+                systems = {st: bs3.System.from_workload(w, st) for st in ("f32", "f64")}
+                y0 = torch.tensor(w.y0, device="cuda")
+                yo = torch.empty_like(y0)
+                rc, _ = bs3.bs3_solve(systems["f64"].handle, w.t0, w.t1, y0, 1e-11, 1e-11, bs3.DOUBLE,
+                                      bs3.ACC_FLOAT2, None, 0, None, yo, 0)
+                if rc != bs3.OK:
+                    continue
+                y_ref = yo.cpu().numpy()
+                for rt in (1e-3, 1e-6, 1e-8):
+                    for variant, store in solvers:
+                        rc, _ = bs3.bs3_solve(systems[store].handle, w.t0, w.t1, y0, rt, rt,
+                                              bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2, None, 0, None, yo, 0)
+                        if rc == bs3.OK:
+                            errs.setdefault((rt, variant), []).append(normalized_error(y_ref, yo.cpu().numpy(), N))
+                for sy in systems.values():
+                    sy.close()
+            for (rt, variant), v in sorted(errs.items()):
+                rec = {"benchmark": bench_name, "N": N, "rtol": rt, "solver": variant, "tests": len(v),
+                       "error_min": min(v), "error_median": float(np.median(v)), "error_max": max(v)}
+                rows.append(rec)
+                print(json.dumps(rec), flush=True)
+    print(json.dumps({"case": name, "reference": "GPU binary64 solve at rtol=atol=1e-11 (GPU-derived)",
+                      "rows": rows}))
+
+
+def run_proposer_case(name):
+    from paper_2605_23727_gb300 import bs3
+    import __graft_entry__
+    __graft_entry__.build()
+    bs3.load()
+    N = 32768 if name == "proposer_lco32768_f16" else 8192
+    print(json.dumps(dict({"case": name}, **proposer_comparison(N))))
 
 
 def run_phases_case(name):
@@ -449,15 +525,6 @@ def run_sweep_case(name):
         s.close()
         curves[f"{variant}/{store}" + ("" if method == "bs32" else "/dp54")] = pts
 
-    def time_at(pts, e):
-        # log-log interpolation between the two points bracketing error e
-        for (e_a, t_a), (e_b, t_b) in zip(pts, pts[1:]):
-            lo, hi = min(e_a, e_b), max(e_a, e_b)
-            if lo <= e <= hi and e_a != e_b:
-                f = (math.log(e) - math.log(e_a)) / (math.log(e_b) - math.log(e_a))
-                return math.exp(math.log(t_a) + f * (math.log(t_b) - math.log(t_a)))
-        return None
-
     summary = []
     for e_target, t_double in curves["double/f64"]:
         row = {"global_error": e_target, "double_ms": t_double}
@@ -470,6 +537,17 @@ def run_sweep_case(name):
     print(json.dumps({"case": name, "time_at_double_error": summary}))
 
 
+def time_at(pts, e):
+    """Time at global error e by log-log interpolation between the two points
+    (error, time) of a curve that bracket e; None when none does."""
+    for (e_a, t_a), (e_b, t_b) in zip(pts, pts[1:]):
+        lo, hi = min(e_a, e_b), max(e_a, e_b)
+        if lo <= e <= hi and e_a != e_b:
+            f = (math.log(e) - math.log(e_a)) / (math.log(e_b) - math.log(e_a))
+            return math.exp(math.log(t_a) + f * (math.log(t_b) - math.log(t_a)))
+    return None
+
+
 def run_case(name):
     if name.startswith("ensemble"):
         return run_ensemble_case(name)
@@ -479,6 +557,8 @@ def run_case(name):
         return run_sweep_case(name)
     if name.startswith("beta"):
         return run_beta_case(name)
+    if name == "size_vs_error":
+        return run_size_case(name)
     if name.startswith("ragged_skewed"):
         return run_skewed_case(name)
     if name == "batch_config4":
@@ -535,6 +615,8 @@ def parse():
     ap.add_argument("--impl", default="bs3", choices=["bs3", "reference"])
     ap.add_argument("--accum", default="float2", choices=["float2", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the accuracy-against-tolerance sweep")
+    ap.add_argument("--no-proposer", action="store_true", help="skip the learned-proposer comparison")
     ap.add_argument("--cpu-sample-attempts", type=int, default=100)
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one solve of a named case and print its stats (profiling runs)")
@@ -807,6 +889,14 @@ def run_gpu(args):
                                       "attempts": std.n_accepted + std.n_rejected,
                                       "global_error": normalized_error(y_ref, y_d.cpu().numpy(), w.N)}
 
+    # ------------------------------------ accuracy against tolerance (Sec. 3.2)
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = accuracy_sweep(bs3, torch, w, y0_d, y_ref, stream, flush, local)
+    proposer_line = None
+    if rank == 0 and not args.no_proposer:
+        proposer_line = proposer_comparison(32768)
+
     # --------------------------------------------------------------- roofline
     evals = st.n_rhs_evals
     bytes_per_eval = w.N * w.N * STORE_BYTES[h_store] + w.N * 4 * 2 + n * 8 * 6
@@ -857,6 +947,8 @@ def run_gpu(args):
         "sigma_d_literal": sigma_literal,
         "survey": survey,
         "dormand_prince_54": dp54,
+        "accuracy_sweep": sweep,
+        "learned_proposer": proposer_line,
         "wall_s_timed_region": wall,
         "clocks": clocks,
         "e2e": {"value": round(statistics.median(e2e_ms), 4), "unit": "ms",
@@ -882,6 +974,60 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(result))
+
+
+SWEEP_RTOLS = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9]
+SWEEP_COMBOS = [("double", "f64"), ("mixed2", "f32"), ("mixed1", "f32"), ("single", "f32")]
+
+
+def accuracy_sweep(bs3, torch, w, y0_d, y_ref, stream, flush, device):
+    """Global error and time-to-solution of each variant over rtol = atol =
+    1e-3 .. 1e-9 on the benchmark workload (Sec. 3.2, Fig. Tol-VS-Error):
+    per rtol, each mixed variant's error as a factor of the binary64 path's,
+    and its time at the binary64 path's error (log-log interpolation along its
+    own curve) as a ratio to the binary64 time.  L2 flushed before each timed
+    solve; each configuration warmed up once."""
+    y_d = torch.empty_like(y0_d)
+    curves, rows = {}, []
+    for variant, store in SWEEP_COMBOS:
+        s = bs3.System(w.kind, w.N, w.params, None, device=device, stream=stream.cuda_stream)
+        s.set_coupling(w.coupling, store)
+        bs3.bs3_solve(s.handle, w.t0, w.t1, y0_d, 1e-3, 1e-3, bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2, None, 0,
+                      None, y_d, 0)
+        pts = []
+        for rt in SWEEP_RTOLS:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, st = bs3.bs3_solve(s.handle, w.t0, w.t1, y0_d, rt, rt, bs3.VARIANT_IDS[variant], bs3.ACC_FLOAT2,
+                                   None, 0, None, y_d, 0)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = normalized_error(y_ref, y_d.cpu().numpy(), w.N) if rc == bs3.OK else None
+            pts.append({"rtol": rt, "status": bs3.bs3_status_string(rc), "ms": round(ms, 3), "global_error": err,
+                        "attempts": st.n_accepted + st.n_rejected})
+        s.close()
+        curves[f"{variant}/{store}"] = pts
+    dbl = curves["double/f64"]
+    for k, rt in enumerate(SWEEP_RTOLS):
+        e_d, t_d = dbl[k]["global_error"], dbl[k]["ms"]
+        row = {"rtol": rt, "double/f64": {"global_error": e_d, "ms": t_d}}
+        for key, pts in curves.items():
+            if key == "double/f64":
+                continue
+            p = pts[k]
+            ok = [(q["global_error"], q["ms"]) for q in pts if q["global_error"] is not None]
+            t = time_at(ok, e_d) if e_d is not None else None
+            row[key] = {"global_error": p["global_error"], "ms": p["ms"],
+                        "error_factor_vs_double": (None if p["global_error"] is None or not e_d
+                                                   else round(p["global_error"] / e_d, 3)),
+                        "ms_at_double_error": None if t is None else round(t, 3),
+                        "speedup_at_double_error": None if t is None else round(t_d / t, 3)}
+        rows.append(row)
+    return {"workload": WORKLOAD, "reference": "oracle DOPRI5 rtol=atol=1e-12", "per_rtol": rows,
+            "curves": curves}
 
 
 def streaming_roofline(bs3, hbm_peak):

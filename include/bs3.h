@@ -367,8 +367,9 @@ typedef struct {
  * by bs3_solve_batch beside the items as bs3_ensemble_solve solves it.  All
  * pointers but the counts are device pointers: K N x N binary32 row-major,
  * omega, theta0, theta_out [T][N] binary64.  n_acc, n_rej, status: host
- * arrays of T (may be NULL).  ctas: CTAs of each stage product (0 = chosen by
- * the call's cost model, see bs3_solve_batch); tile_n as
+ * arrays of T (may be NULL).  ctas: 0 = the group's products use every SM,
+ * after the items' launch; > 0 = the group runs beside the items with this
+ * many CTAs per product (see bs3_solve_batch); tile_n as
  * bs3_ensemble_solve_tiled. */
 typedef struct {
     const float* K;
@@ -398,16 +399,17 @@ typedef struct {
  * The items run as bs3_batch_solve runs its systems: one cooperative launch,
  * largest systems first, systems too large for one SM's share solved by teams
  * of CTAs, the others whole by single CTAs, each CTA taking systems from a work
- * queue.  The group runs as one graph whose attempt loop is a conditional
- * node decided on the device.  With both, the items' launch and the group's
- * graph are one CUDA graph with two branches on disjoint CTA budgets: the group's
- * products get group->ctas CTAs (0: SMs x its share of the estimated work per
- * attempt, the tensor-core products at 1 PFLOP/s against the items' weight
- * streams at 30 GB/s per CTA), the items the remaining SMs.  Items' weights
- * are the systems' stored copies; the call allocates a small descriptor
- * block and, once per system, a state buffer the system keeps.  Waits for
- * completion; *kernel_ms (may be NULL) receives the device time of the
- * solve.  Returns the first non-OK item status, else the group's, else
+ * queue.  The group runs as bs3_ensemble_solve runs it, its attempt loop a
+ * conditional graph node decided on the device.  With both, they form one
+ * CUDA graph, launched once: by default the items' launch, then the group,
+ * each on every SM (a solver CTA holds all of an SM's registers, so the two
+ * cannot share SMs, and a split of the SMs cannot finish before the sum of the
+ * two parts); with group->ctas > 0 the two run side by side, the group's
+ * products on group->ctas CTAs and the items on the other SMs.  Items'
+ * weights are the systems' stored copies; the call allocates a small
+ * descriptor block and, once per system, a state buffer the system keeps.
+ * Waits for completion; *kernel_ms (may be NULL) receives the device time of
+ * the solve.  Returns the first non-OK item status, else the group's, else
  * BS3_OK; BS3_ERR_INVALID_ARG for mixed kinds, types or devices. */
 int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int accum, int flags,
                     bs3_ensemble_group* group, int device, void* stream, double* kernel_ms);

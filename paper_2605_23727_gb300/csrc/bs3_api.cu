@@ -1095,22 +1095,13 @@ int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int acc
       st = own;
     }
     if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
-    if (group && S > 0) {
-      if (group->ctas > 0) {
-        g_ctas = std::min(group->ctas, sms - 1);
-      } else {
-        // estimated work per attempt: the group's three split-product stages
-        // at ~1 PFLOP/s, each item's three weight streams at ~30 GB/s per CTA
-        const double g_us = 9.0 * 2.0 * (double)group->N * group->N * 2.0 * group->T / 1.0e9;
-        double i_us = 0.0;
-        for (int64_t k = 0; k < S; ++k) {
-          const double n = (double)items[k].sys->N;
-          i_us += kAttemptFixedUs + 3.0 * n * n * (double)store_bytes(s0->store) / kCtaStreamBytesPerUs;
-        }
-        i_us /= sms;   // the items spread over the SMs
-        g_ctas = (int)std::lround(sms * g_us / (g_us + i_us));
-      }
-      g_ctas = std::max(1, std::min(g_ctas, sms - 1));
+    // group->ctas > 0 with items: the two run side by side on disjoint CTA
+    // budgets; otherwise one after the other, each on the whole GPU (a solver
+    // CTA holds all of an SM's registers, so the two never share an SM and a
+    // split cannot finish sooner than the sum of the two parts)
+    const bool side_by_side = group && S > 0 && group->ctas > 0;
+    if (side_by_side) {
+      g_ctas = std::max(1, std::min(group->ctas, sms - 1));
       i_ctas = sms - g_ctas;
     } else if (group) {
       g_ctas = group->ctas > 0 ? std::min(group->ctas, sms) : sms;
@@ -1211,24 +1202,28 @@ int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int acc
       if (cudaEventRecord(ev0, st) != cudaSuccess || cudaLaunchKernelExC(&cfg, bkern, kargs) != cudaSuccess ||
           cudaEventRecord(ev1, st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
     } else {
-      if (S > 0 && (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
+      if (side_by_side && (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)) {
         rc = BS3_ERR_CUDA;
         break;
       }
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
       cudaError_t ce = cudaSuccess;
-      if (S > 0) {
+      if (side_by_side) {
         // the items' launch on a branch of its own
         ce = cudaEventRecord(fork, st);
         if (ce == cudaSuccess) ce = cudaStreamWaitEvent(side, fork, 0);
         cfg.stream = side;
         if (ce == cudaSuccess) ce = cudaLaunchKernelExC(&cfg, bkern, kargs);
         if (ce == cudaSuccess) ce = cudaEventRecord(join, side);
+      } else if (S > 0) {
+        // the items' launch first, then the group, in the same graph
+        cfg.stream = st;
+        ce = cudaLaunchKernelExC(&cfg, bkern, kargs);
       }
       int crc = ce == cudaSuccess ? run->capture(st, body, nullptr, nullptr) : BS3_ERR_CUDA;
-      if (S > 0 && crc == BS3_OK && cudaStreamWaitEvent(st, join, 0) != cudaSuccess) crc = BS3_ERR_CUDA;
+      if (side_by_side && crc == BS3_OK && cudaStreamWaitEvent(st, join, 0) != cudaSuccess) crc = BS3_ERR_CUDA;
       const cudaError_t ee = cudaStreamEndCapture(st, &graph);
       if (crc != BS3_OK || ee != cudaSuccess) { rc = crc != BS3_OK ? crc : BS3_ERR_CUDA; break; }
       if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess || cudaEventRecord(ev0, st) != cudaSuccess ||

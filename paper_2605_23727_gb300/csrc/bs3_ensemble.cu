@@ -104,9 +104,10 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
   return __longlong_as_double(x > y ? x : y);
 }
 
-// sin and cos of a binary64 phase, rounded to binary32: the reduction of the
-// solver's sincos_f_of_d (two-constant Cody-Waite on 2 pi in binary64), with
-// the reduced phase converted by d2f
+// sin and cos of a binary64 phase in binary32: two-constant Cody-Waite
+// reduction on 2 pi in binary64, the reduced phase converted by d2f, then the
+// library sincosf (a few ulp; the bfloat16 split of the ensembles' operand
+// keeps 16 bits, far above that)
 __device__ __forceinline__ void sincos_phase(double th, float* s, float* c) {
   const double kInv2Pi = 0.15915494309189535;
   const double k2PiHi = 6.2831853069365025;             // 2 pi rounded to 33 bits
@@ -581,7 +582,7 @@ int EnsembleRunT<BNT>::capture(cudaStream_t st, cudaStream_t body, cudaEvent_t l
   cudaGraphConditionalHandle h;
   EN_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 0, 0));
   ens_loop_start<<<1, 1, 0, st>>>(h, a.tr.any_live, derr, iters);
-  if (loop_begin) EN_CUDA(cudaEventRecord(loop_begin, st));
+  if (loop_begin) EN_CUDA(cudaEventRecordWithFlags(loop_begin, st, cudaEventRecordExternal));
   EN_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
   cp.conditional.handle = h;
@@ -617,7 +618,7 @@ int EnsembleRunT<BNT>::capture(cudaStream_t st, cudaStream_t body, cudaEvent_t l
   cudaGraph_t ended = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(body, &ended);
   if (eb != cudaSuccess || ee != cudaSuccess) return BS3_ERR_CUDA;
-  if (loop_end) EN_CUDA(cudaEventRecord(loop_end, st));
+  if (loop_end) EN_CUDA(cudaEventRecordWithFlags(loop_end, st, cudaEventRecordExternal));
   ens_gather<<<ew_blocks, 256, 0, st>>>(a, theta_out);
   EN_CUDA(cudaGetLastError());
   return BS3_OK;
@@ -677,8 +678,8 @@ namespace {
 
 // A standalone ensemble solve: one graph (set-up stages, the attempt loop as a
 // device-decided WHILE node, the gather), launched once; the host waits only
-// for its end.  loop_ms (optional) receives the device time of the attempt
-// loop alone.
+// for its end.  loop_ms (optional) receives the device time of the graph (the
+// two set-up stage products, the attempt loop and the gather).
 int ensemble_solve_graph(const EnsembleSpec& sp, int64_t* n_acc, int64_t* n_rej, int32_t* status,
                          int64_t* lockstep_attempts, cudaStream_t st_in, float* loop_ms) {
   cudaStream_t st = st_in, own = nullptr, body = nullptr;
@@ -701,11 +702,12 @@ int ensemble_solve_graph(const EnsembleSpec& sp, int64_t* n_acc, int64_t* n_rej,
     rc = ensemble_create(sp, st, &run);
     if (rc != BS3_OK) break;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
-    rc = run->capture(st, body, ev0, ev1);
+    rc = run->capture(st, body, nullptr, nullptr);
     const cudaError_t ee = cudaStreamEndCapture(st, &graph);
     if (rc != BS3_OK) break;
     if (ee != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess ||
-        cudaGraphLaunch(exec, st) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
+        (ev0 && cudaEventRecord(ev0, st) != cudaSuccess) || cudaGraphLaunch(exec, st) != cudaSuccess ||
+        (ev1 && cudaEventRecord(ev1, st) != cudaSuccess)) { rc = BS3_ERR_CUDA; break; }
     rc = run->finish(n_acc, n_rej, status, lockstep_attempts);
     if (loop_ms && cudaEventElapsedTime(loop_ms, ev0, ev1) != cudaSuccess && rc == BS3_OK) rc = BS3_ERR_CUDA;
   } while (0);

@@ -24,8 +24,10 @@ struct EnsembleSpec {
 // buffer and sets up the initial state (waits for that set-up); capture()
 // records every kernel of the solve into the capture in progress on `st`
 // (set-up stages, the attempt loop as a conditional WHILE node whose body is
-// captured on `body`, then the gather of the final phases); after the graph
-// has run, finish() reads the counts and returns the solve's status.
+// captured on `body`, then the gather of the final phases; loop_begin and
+// loop_end, when not null, become event-record nodes around the loop); after
+// the graph has run, finish() reads the counts and returns the solve's
+// status.
 class EnsembleRun {
  public:
   virtual ~EnsembleRun() {}

@@ -79,9 +79,10 @@ def test_group_alone_equals_the_ensemble_entry():
 
 @pytest.mark.parametrize("ctas", [0, 40])
 def test_items_and_group_in_one_submission(ctas):
-    """Systems and a group together (one graph, two branches on disjoint CTA
-    budgets): the group as bs3_ensemble_solve computes it, sampled trajectories
-    against the oracle's tensor variant, each system against its oracle solve."""
+    """Systems and a group together in one graph (ctas = 0: one after the
+    other on every SM; ctas = 40: side by side on disjoint CTA budgets): the
+    group as bs3_ensemble_solve computes it, sampled trajectories against the
+    oracle's tensor variant, sampled systems against their oracle solves."""
     bs3 = library()
     torch = torch_cuda()
     systems = W.lco_ragged_batch(count=40, n_min=16, n_max=400, seed=32, t1=4.0)
