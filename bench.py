@@ -64,6 +64,7 @@ CASES = {
     "kuramoto4096_mixed1_f32": (lambda: workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL), "mixed1", "f32"),
     "kuramoto4096_mixed1_bf16": (lambda: workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL), "mixed1", "bf16"),
     "kuramoto4096_double_f64": (lambda: workloads.kuramoto(4096, 0, t1=5.0, rtol=RTOL), "double", "f64"),
+    "kuramoto4096_mixed2_f32": (lambda: workloads.kuramoto(4096, 0, t1=T1, rtol=RTOL), "mixed2", "f32"),
     "lco16384_mixed1_f16": (lambda: workloads.lco_config(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "f16"),
     "lco32768_mixed1_f16": (lambda: workloads.lco_config(32768, 0, t1=0.2, rtol=RTOL), "mixed1", "f16"),
     "circadian16384_mixed1_bf16": (lambda: workloads.circadian(16384, 0, t1=0.5, rtol=RTOL), "mixed1", "bf16"),

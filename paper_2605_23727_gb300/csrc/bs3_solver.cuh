@@ -397,7 +397,8 @@ struct RowPar {
 
 template <int KIND>
 __device__ __forceinline__ void finish(const Args& a, const RowPar& rp, const double* Y, double s0, double s1,
-                                       Prec p, bool single, double* K, const float2* cached = nullptr) {
+                                       Prec p, bool single, double* K, const float2* cached = nullptr,
+                                       const double2* cached64 = nullptr) {
   if (KIND == K_KURAMOTO) {
     if (p.s == 0) {
       const float sc = rp.scale;
@@ -417,7 +418,12 @@ __device__ __forceinline__ void finish(const Args& a, const RowPar& rp, const do
       const double sc = (double)rp.scale;
       const double S = s0 * sc, C = s1 * sc;
       double si, ci;
-      sincos(Y[0], &si, &ci);
+      if (cached64) {   // the same values, computed while the previous barrier waited
+        si = cached64->x;
+        ci = cached64->y;
+      } else {
+        sincos(Y[0], &si, &ci);
+      }
       const double cpl = ci * S - si * C;
       K[0] = p.f == 0 ? (double)((float)rp.par + (float)cpl) : rp.par + cpl;
     }
@@ -509,6 +515,8 @@ struct Ctx {
   double* srs;        // shared row sums
   float* sscale;      // shared row scales
   float2* sisc;       // shared binary32 (sin, cos) of each row's last j-vector (Kuramoto), or null
+  double2* sisc64;    // shared binary64 (sin, cos) of each row's stage argument (Kuramoto), or null
+  bool have64;        // sisc64 holds this stage's values
   int rc, rb, nr;
   int rank, nb;      // this CTA's place in the group of CTAs that solves the system (nb = 1: alone)
   int iX, iXn, iK1, iK2, iK3, iK4;
@@ -651,7 +659,8 @@ __device__ __forceinline__ void epilogue(const Args& a, Ctx& x, int phase, int l
       default: Y[c] = xo; break;   // PH_RHS, PH_K1
     }
   }
-  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K, x.sisc ? x.sisc + li : nullptr);
+  finish<KIND>(a, rp, Y, s0, s1, x.p, x.single, K, x.sisc ? x.sisc + li : nullptr,
+               x.have64 ? x.sisc64 + li : nullptr);
   switch (phase) {
     case PH_RHS:
 #pragma unroll
@@ -814,10 +823,10 @@ __device__ __forceinline__ double ld_bits(const unsigned long long* p) {
 
 // Shared-memory bytes of a launch: the state slots [slots][d][rc] (six for
 // Bogacki-Shampine, nine for Dormand-Prince) plus per-agent
-// parameters (three binary64 and one binary32 per agent) and a binary32
-// (sin, cos) pair per agent.
+// parameters (three binary64 and one binary32 per agent), a binary32
+// (sin, cos) pair and a binary64 (sin, cos) pair per agent.
 __host__ __device__ constexpr size_t state_smem_bytes(int d, int rc, int slots = 6) {
-  return (size_t)rc * (slots * d * 8 + 3 * 8 + 4 + 8) + 16;
+  return (size_t)rc * (slots * d * 8 + 3 * 8 + 4 + 8 + 16) + 32;
 }
 
 
@@ -854,6 +863,43 @@ __device__ __forceinline__ bool sync_all(const Ctx& x, Control* c, unsigned long
     return true;
   }
   return grid_sync(c, target, x.nb, spin_limit, s_abort);
+}
+
+// The same barrier, with work that the threads outside warp 0 do while thread
+// 0 arrives and waits for the other CTAs (work(k, nk): share k of nk).
+template <class W>
+__device__ __forceinline__ bool sync_all_with(const Ctx& x, Control* c, unsigned long long& target,
+                                              long long spin_limit, int* s_abort, W&& work) {
+  if (x.nb == 1) {
+    __syncthreads();
+    work((int)threadIdx.x, (int)blockDim.x);
+    __syncthreads();
+    return true;
+  }
+  __syncthreads();
+  target += x.nb;
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" :: "l"(&c->bar) : "memory");
+    long long it = 0;
+    int abort = 0;
+    while (true) {
+      const unsigned long long v = ld_acquire_u64(&c->bar);
+      if (v >= kAbortBias) { abort = 1; break; }
+      if (v >= target) break;
+      if (++it > spin_limit) {
+        atomicCAS(&c->status, 0, (int)S_DEVICE_WAIT);
+        atomicAdd(&c->bar, kAbortBias);
+        abort = 1;
+        break;
+      }
+      if (it > 256) __nanosleep(32);
+    }
+    *s_abort = abort;
+  } else if (threadIdx.x >= 32) {
+    work((int)threadIdx.x - 32, (int)blockDim.x - 32);
+  }
+  __syncthreads();
+  return !*s_abort;
 }
 
 // A job (RHS, one attempt or a whole solve) on the agents [x.rb, x.rb + x.nr)
@@ -1004,17 +1050,18 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
       if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) break;
       if (rec) ts[1] = globaltimer_ns();
       if (leader) ctrl->emax[parity ^ 1] = 0ull;
+      // the host's cancel flag, read now and latched after the last stage
+      // (the host-memory read overlaps the stages instead of delaying one)
+      const int cancel_v = (leader && a.cancel) ? *a.cancel : 0;
       for (int l = 2; l <= 7; ++l) {
         x.p = variant_prec_dp(a.variant, l);
         x.pn = variant_prec_dp(a.variant, l < 7 ? l + 1 : 7);
-        if (l == 7) {
-          if (leader) {
-            ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
-            if (a.progress) *a.progress = sc.t;
-          }
-          x.m1 = 0.0;
-        }
+        if (l == 7) x.m1 = 0.0;
         stage<KIND, ST>(a, x, PH_D2 + l - 2, l & 1, s_grp);
+        if (l == 7 && leader) {
+          ctrl->cancel_seen[parity] = cancel_v;
+          if (a.progress) *a.progress = sc.t;
+        }
         if (l == 7) block_max(x.m1, &ctrl->emax[parity], s_red);
         if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
         if (rec && (l == 3 || l == 5)) ts[l == 3 ? 2 : 3] = globaltimer_ns();
@@ -1028,27 +1075,60 @@ __device__ __forceinline__ void run_job(const Args& a, Ctx& x, Scal& sc, int* s_
             Y[c] = axpy_state(sv<KIND>(x, x.iX, c, li), x.c21, sv<KIND>(x, x.iK1, c, li), single);
           put_jv<KIND>(a, 0, x.rb + li, Y, p2.g, single, x.sisc ? x.sisc + li : nullptr);
         }
-        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        // binary64 sin/cos of a Sigma = D stage's argument for its i-side
+        // finish, computed while the barrier before the stage waits
+        const bool c2 = KIND == K_KURAMOTO && x.sisc64 != nullptr && p2.s == 1;
+        const bool c3 = KIND == K_KURAMOTO && x.sisc64 != nullptr && p3.s == 1;
+        const bool c4 = KIND == K_KURAMOTO && x.sisc64 != nullptr && p4.s == 1;
+        if (!sync_all_with(x, ctrl, bt, a.spin_limit, s_abort, [&](int k, int nk) {
+              if (c2)
+                for (int li = k; li < x.nr; li += nk) {
+                  double s, c;
+                  sincos(axpy_state(sv<KIND>(x, x.iX, 0, li), x.c21, sv<KIND>(x, x.iK1, 0, li), single), &s, &c);
+                  x.sisc64[li] = make_double2(s, c);
+                }
+            })) { aborted = true; break; }
         if (rec) ts[1] = globaltimer_ns();
+        // the host's cancel flag, read now and latched after stage 4 (the
+        // host-memory read overlaps stages 2 to 4 instead of delaying one)
+        const int cancel_v = (leader && a.cancel) ? *a.cancel : 0;
         // ---- B2: K2 = f(Y2); Y3 -> j-vector 1
         if (leader) ctrl->emax[parity ^ 1] = 0ull;
         x.p = p2; x.pn = p3;
+        x.have64 = c2;
         stage<KIND, ST>(a, x, PH_B2, 0, s_grp);
-        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (!sync_all_with(x, ctrl, bt, a.spin_limit, s_abort, [&](int k, int nk) {
+              if (c3)
+                for (int li = k; li < x.nr; li += nk) {
+                  double s, c;
+                  sincos(axpy_state(sv<KIND>(x, x.iX, 0, li), x.c32, sv<KIND>(x, x.iK2, 0, li), single), &s, &c);
+                  x.sisc64[li] = make_double2(s, c);
+                }
+            })) { aborted = true; break; }
         if (rec) ts[2] = globaltimer_ns();
         // ---- B3: K3 = f(Y3); X' -> j-vector 2
         x.p = p3; x.pn = p4;
+        x.have64 = c3;
         stage<KIND, ST>(a, x, PH_B3, 1, s_grp);
-        if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
+        if (!sync_all_with(x, ctrl, bt, a.spin_limit, s_abort, [&](int k, int nk) {
+              if (c4)
+                for (int li = k; li < x.nr; li += nk) {
+                  double s, c;
+                  sincos(sv<KIND>(x, x.iXn, 0, li), &s, &c);
+                  x.sisc64[li] = make_double2(s, c);
+                }
+            })) { aborted = true; break; }
         if (rec) ts[3] = globaltimer_ns();
         // ---- B4: K4 = f(X'); error norm
-        if (leader) {
-          ctrl->cancel_seen[parity] = a.cancel ? *a.cancel : 0;
-          if (a.progress) *a.progress = sc.t;
-        }
         x.p = p4;
         x.m1 = 0.0;
+        x.have64 = c4;
         stage<KIND, ST>(a, x, PH_B4, 2, s_grp);
+        x.have64 = false;
+        if (leader) {
+          ctrl->cancel_seen[parity] = cancel_v;
+          if (a.progress) *a.progress = sc.t;
+        }
         block_max(x.m1, &ctrl->emax[parity], s_red);
         if (!sync_all(x, ctrl, bt, a.spin_limit, s_abort)) { aborted = true; break; }
       } while (false);
@@ -1219,6 +1299,8 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   x.srs = x.sth + x.rc;
   x.sscale = (float*)(x.srs + x.rc);
   x.sisc = (float2*)(((uintptr_t)(x.sscale + x.rc) + 7) & ~(uintptr_t)7);
+  x.sisc64 = (double2*)(((uintptr_t)(x.sisc + x.rc) + 15) & ~(uintptr_t)15);
+  x.have64 = false;
   x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
   x.iK7 = 8;   // Dormand-Prince: K_l in slot l + 1 (nine slots)
   x.rtol = a.rtol;
@@ -1356,6 +1438,8 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum) + x.rb;   // read only by the circadian kind
   x.sscale = const_cast<float*>(D.scale) + x.rb;
   x.sisc = nullptr;
+  x.sisc64 = nullptr;
+  x.have64 = false;
   x.iX = 0; x.iXn = 1; x.iK1 = 2; x.iK2 = 3; x.iK3 = 4; x.iK4 = 5;
   x.rtol = a.rtol;
   x.thr = a.atol / a.rtol;
