@@ -945,6 +945,9 @@ def run_gpu(args):
         "speedup_vs_fp64_gpu": survey["double/f64"]["ms"] / ms,
         "accepted": st.n_accepted, "rejected": st.n_rejected, "rhs_evals": evals,
         "headline_within_error_factor": bool(survey[head]["global_error"] <= ERROR_FACTOR * e_double),
+        "parity_unpinned": ["step-size controller formula and constants (the paper gives none; the standard "
+                            "3(2) controller with exponent 1/3 and safety 0.8 is read in)",
+                            "starting step (the paper gives none; Hairer-Norsett-Wanner II.4 is read in)"],
         "sigma_d_literal": sigma_literal,
         "survey": survey,
         "dormand_prince_54": dp54,

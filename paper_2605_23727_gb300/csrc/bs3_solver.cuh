@@ -328,6 +328,11 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
   }
   // the weight chunks of the next iteration are loaded before the current
   // one's arctangents run, so the stream's latency hides behind them
+  // the float-float sum of a Sigma = D stage runs as a packed TwoSum over the
+  // even and odd columns of each row (two accumulators, merged after the loop)
+  unsigned long long hi2[RB], lo2[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) hi2[r] = lo2[r] = 0ull;
   uint4 nxt[RB];
   {
     const int col = lt * VEC;
@@ -365,8 +370,17 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
         for (int e = 0; e < VEC; e += 2) {
           float a0, a1;
           atan_f32x2(__fsub_rn(xj[e], xi32[r]), __fsub_rn(xj[e + 1], xi32[r]), a0, a1);
-          acc[r][0].add_f(L::f(raw[r], e), a0);
-          acc[r][0].add_f(L::f(raw[r], e + 1), a1);
+          if (MODE == M_SD2 && VEC <= 8) {
+            const unsigned long long pr = mul2(pk2(L::f(raw[r], e), L::f(raw[r], e + 1)), pk2(a0, a1));
+            const unsigned long long sm = add2(hi2[r], pr);
+            const unsigned long long bb = sub2(sm, hi2[r]);
+            const unsigned long long er = add2(sub2(hi2[r], sub2(sm, bb)), sub2(pr, bb));
+            hi2[r] = sm;
+            lo2[r] = add2(lo2[r], er);
+          } else {
+            acc[r][0].add_f(L::f(raw[r], e), a0);
+            acc[r][0].add_f(L::f(raw[r], e + 1), a1);
+          }
         }
     } else {
       double xj[VEC];
@@ -377,6 +391,16 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
 #pragma unroll
         for (int e = 0; e < VEC; ++e)
           acc[r][0].add_d(L::get_d(raw[r], e), atan(__dsub_rn(xj[e], xi64[r])));
+    }
+  }
+  if (MODE == M_SD2 && VEC <= 8) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      float e0, e1, l0, l1, s_, er;
+      upk2(hi2[r], e0, e1);
+      upk2(lo2[r], l0, l1);
+      two_sum(e0, e1, s_, er);
+      set_packed(acc[r][0], s_, __fadd_rn(__fadd_rn(l0, l1), er));
     }
   }
 #pragma unroll
