@@ -6,7 +6,7 @@ import pytest
 
 import workloads as W
 from oracle import bs3 as obs3
-from oracle import metrics, models
+from oracle import models
 from tests.gpu_helpers import library, torch_cuda
 
 pytestmark = pytest.mark.gpu
@@ -26,25 +26,37 @@ def _ensemble(N, T, t1, rtol, seed):
 
 
 def test_ensemble_matches_oracle_per_trajectory():
-    N, T, t1, rtol = 256, 128, 10.0, 1e-6
-    K, omega, theta0, y, n_acc, n_rej, status, steps = _ensemble(N, T, t1, rtol, 3)
+    """Per trajectory against the oracle's tensor variant solved alone: over
+    t in [0, 10] the attempt counts agree within 5 %; over t in [0, 0.5] the
+    final phases agree within the bound derived from the one place the two
+    differ (the tensor cores round each of the 3N/16 accumulations of an
+    output toward zero, at most one binary32 ulp of a running sum bounded by
+    R_i = sum_j |K_ij|; the coupling then differs by at most
+    d = 2 (3N/16) 2^-23 max_i R_i, and the phases by d (e^{L t} - 1) / L with
+    the Lipschitz constant L = 2 max_i R_i)."""
+    N, T, rtol = 256, 128, 1e-6
+    K, omega, theta0, y, n_acc, n_rej, status, steps = _ensemble(N, T, 10.0, rtol, 3)
     assert np.all(status == 0) and np.all(np.isfinite(y))
     assert steps >= np.max(n_acc + n_rej)
+    for b in (0, 63, 127):
+        osys = models.make_system("kuramoto", N, omega[b], K, "f32")
+        ref = obs3.solve(osys, 0.0, 10.0, theta0[b], rtol, rtol, "tensor")
+        n_gpu, n_ref = n_acc[b] + n_rej[b], ref.n_accepted + ref.n_rejected
+        assert abs(n_gpu - n_ref) <= max(2, 0.05 * n_ref), (b, n_gpu, n_ref)
+    t1 = 0.5
+    K, omega, theta0, y, n_acc, n_rej, status, steps = _ensemble(N, T, t1, rtol, 3)
+    R = float(np.max(np.abs(K.astype(np.float64)).sum(axis=1)))
+    d = 2.0 * (3 * N / 16) * 2.0 ** -23 * R
+    L = 2.0 * R
+    bound = d * (np.exp(L * t1) - 1.0) / L
     for b in (0, 63, 127):
         osys = models.make_system("kuramoto", N, omega[b], K, "f32")
         ref = obs3.solve(osys, 0.0, t1, theta0[b], rtol, rtol, "tensor")
         n_gpu, n_ref = n_acc[b] + n_rej[b], ref.n_accepted + ref.n_rejected
         assert abs(n_gpu - n_ref) <= max(2, 0.05 * n_ref), (b, n_gpu, n_ref)
-        # the tensor cores accumulate each 16-wide step in binary32 with a bias
-        # toward zero (about 0.5 ulp of the running sum per instruction; the
-        # oracle sums exactly, then rounds), so compare global errors against a
-        # tight binary64 solve of the same trajectory instead of the solutions
-        tight = obs3.solve(models.make_system("kuramoto", N, omega[b], K, "f64"), 0.0, t1, theta0[b],
-                           1e-10, 1e-10, "double")
-        e_gpu = metrics.normalized_final_error(tight.y, y[b], N)
-        e_tensor = metrics.normalized_final_error(tight.y, ref.y, N)
-        print(f"trajectory {b}: global error gpu {e_gpu:.3e}, oracle tensor variant {e_tensor:.3e}")
-        assert e_gpu <= 20.0 * e_tensor + 1e-6, (b, e_gpu, e_tensor)
+        dev = float(np.max(np.abs(y[b] - ref.y)))
+        print(f"trajectory {b}: max |dtheta| {dev:.3e} (bound {bound:.3e})")
+        assert dev <= bound, (b, dev, bound)
 
 
 def test_ensemble_trajectories_are_independent():
