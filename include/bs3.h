@@ -392,7 +392,8 @@ typedef struct {
  * != NULL) one shared-K trajectory group.  The items' systems must all be of
  * one kind and one stored weight type, on `device`, with the Bogacki-Shampine
  * pair (bs3_set_method), and circadian systems must share the eight
- * constants.  variant and accum apply to every item (the group runs the
+ * constants; a system appears in at most one item (its buffers hold the item's
+ * state during the solve).  variant and accum apply to every item (the group runs the
  * tensor-core variant of bs3_ensemble_solve).  flags: BS3_HOST_IO if the
  * items' y0 and y_final are host pointers.
  *

@@ -1061,6 +1061,13 @@ int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int acc
       for (int q = 0; q < 8; ++q)
         if (s->g[q] != s0->g[q]) return BS3_ERR_INVALID_ARG;
   }
+  {
+    // an item's system buffers hold its state during the solve: one system per item
+    std::vector<const bs3_system*> seen(n_items);
+    for (int64_t k = 0; k < n_items; ++k) seen[k] = items[k].sys;
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return BS3_ERR_INVALID_ARG;
+  }
   if (group && (!group->K || !group->omega || !group->theta0 || !group->theta_out || group->ctas < 0))
     return BS3_ERR_INVALID_ARG;
   DeviceGuard guard(device);

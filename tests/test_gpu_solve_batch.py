@@ -130,6 +130,8 @@ def test_mixed_kinds_or_types_are_refused():
     assert rc == bs3.ERR_INVALID_ARG
     rc, stats, _, _ = bs3.bs3_solve_batch(items_a + items_c, bs3.MIXED1, bs3.ACC_FLOAT2)
     assert rc == bs3.ERR_INVALID_ARG
+    rc, stats, _, _ = bs3.bs3_solve_batch(items_a + items_a, bs3.MIXED1, bs3.ACC_FLOAT2)
+    assert rc == bs3.ERR_INVALID_ARG      # one system in two items
     bad = dict(items_a[0], rtol=0.0)
     rc, stats, _, _ = bs3.bs3_solve_batch([bad], bs3.MIXED1, bs3.ACC_FLOAT2)
     assert rc == bs3.ERR_INVALID_ARG and stats[0].status == bs3.ERR_INVALID_ARG
