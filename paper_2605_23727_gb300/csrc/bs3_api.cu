@@ -34,6 +34,7 @@ struct bs3_system {
   double* par = nullptr;
   double* theta_h = nullptr;
   double* rowsum = nullptr;
+  float* bias = nullptr;       // row_bias of sum_j |q_ij| per row
   double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // stored weights
   void* q = nullptr;
@@ -175,11 +176,12 @@ __global__ void quantize_kernel(const Src* __restrict__ K, int64_t N, int64_t ld
   }
 }
 
-// rowsum_i = s_i * sum_j q_ij in binary64 (paper-form oscillators).
+// rowsum_i = s_i * sum_j q_ij in binary64 (paper-form oscillators) and
+// bias_i = row_bias(sum_j |q_ij|) (the start of the Kuramoto float-float sums).
 __global__ void rowsum_kernel(const void* __restrict__ q, int st, int64_t N, int64_t ld,
-                              const float* __restrict__ s, double* __restrict__ out) {
+                              const float* __restrict__ s, double* __restrict__ out, float* __restrict__ bias) {
   const int64_t i = blockIdx.x;
-  double acc = 0.0;
+  double acc = 0.0, aacc = 0.0;
   for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
     double v;
     const int64_t e = i * ld + j;
@@ -194,16 +196,27 @@ __global__ void rowsum_kernel(const void* __restrict__ q, int st, int64_t N, int
       }
     }
     acc += v;
+    aacc += fabs(v);
   }
-  __shared__ double sm[32];
+  __shared__ double sm[32], sa[32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  for (int off = 16; off > 0; off >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    aacc += __shfl_xor_sync(0xffffffffu, aacc, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = acc;
+    sa[threadIdx.x >> 5] = aacc;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sm[w];
+    double r = 0.0, ra = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      r += sm[w];
+      ra += sa[w];
+    }
     out[i] = (double)s[i] * r;
+    bias[i] = row_bias(ra);
   }
 }
 
@@ -307,6 +320,7 @@ void fill_args(const bs3_system* s, Args& a) {
   a.q = s->q;
   a.scale = s->scale;
   a.rowsum = s->rowsum;
+  a.bias = s->bias;
   a.par = s->par;
   a.theta_h = s->theta_h;
   for (int k = 0; k < 8; ++k) a.g[k] = s->g[k];
@@ -432,6 +446,7 @@ int bs3_create_system(int kind, int64_t N, const double* params, int64_t n_param
       return fail(BS3_ERR_CUDA);
   }
   if (cudaMalloc(&s->rowsum, N * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
+  if (cudaMalloc(&s->bias, N * sizeof(float)) != cudaSuccess) return fail(BS3_ERR_CUDA);
   if (cudaMalloc(&s->scale, N * sizeof(float)) != cudaSuccess) return fail(BS3_ERR_CUDA);
   if (cudaMalloc(&s->X, dN * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
   if (cudaMalloc(&s->Xn, dN * sizeof(double)) != cudaSuccess) return fail(BS3_ERR_CUDA);
@@ -489,7 +504,7 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
   const size_t eb = store_bytes(store);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) / 256 * 256; return o; };
-  const size_t oQ = take((size_t)offQ[S] * eb), oScale = take(TN * 4), oRow = take(TN * 8), oPar = take(TN * 8),
+  const size_t oQ = take((size_t)offQ[S] * eb), oScale = take(TN * 4), oRow = take(TN * 8), oBias = take(TN * 4), oPar = take(TN * 8),
                oTh = take(TN * 8), oY0 = take((size_t)d * TN * 8), oYF = take((size_t)d * TN * 8),
                oState = take((size_t)6 * d * TN * 8), oJ32 = take((size_t)6 * offL[S] * 4),
                oJ64 = take((size_t)6 * offL[S] * 8), oCtl = take((size_t)S * sizeof(Control)),
@@ -548,7 +563,8 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
       row_amax_kernel<float><<<(unsigned)N, 256, 0, st>>>(kdev, N, amax);
       scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(amax, N, store, sc);
       quantize_kernel<float><<<blocks, 256, 0, st>>>(kdev, N, ld, store, 0, sc, q);
-      rowsum_kernel<<<(unsigned)N, 256, 0, st>>>(q, store, N, ld, sc, (double*)(arena + oRow) + offN[k]);
+      rowsum_kernel<<<(unsigned)N, 256, 0, st>>>(q, store, N, ld, sc, (double*)(arena + oRow) + offN[k],
+                                                 (float*)(arena + oBias) + offN[k]);
       if (cudaGetLastError() != cudaSuccess) rc = BS3_ERR_CUDA;
     }
     if (rc != BS3_OK) break;
@@ -563,6 +579,7 @@ int bs3_batch_solve(int kind, int64_t S, const int64_t* Ns, const double* params
       D.q = arena + oQ + (size_t)offQ[k] * eb;
       D.scale = (const float*)(arena + oScale) + offN[k];
       D.rowsum = (const double*)(arena + oRow) + offN[k];
+      D.bias = (const float*)(arena + oBias) + offN[k];
       D.par = (const double*)(arena + oPar) + offN[k];
       D.theta_h = (kind == BS3_CIRCADIAN) ? (const double*)(arena + oTh) + offN[k] : nullptr;
       D.y0 = (const double*)(arena + oY0) + (size_t)d * offN[k];
@@ -800,6 +817,7 @@ int bs3_destroy_system(bs3_system_t s) {
   cudaFree(s->par);
   cudaFree(s->theta_h);
   cudaFree(s->rowsum);
+  cudaFree(s->bias);
   cudaFree(s->q);
   cudaFree(s->scale);
   cudaFree(s->X);
@@ -855,7 +873,7 @@ int bs3_set_coupling(bs3_system_t s, const void* K, int src, int store, int is_d
       scale_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s->stream>>>(amax, N, store, s->scale);
       quantize_kernel<float><<<blocks, 256, 0, s->stream>>>((const float*)dK, N, ld, store, 0, s->scale, s->q);
     }
-    rowsum_kernel<<<(unsigned)N, 256, 0, s->stream>>>(s->q, store, N, ld, s->scale, s->rowsum);
+    rowsum_kernel<<<(unsigned)N, 256, 0, s->stream>>>(s->q, store, N, ld, s->scale, s->rowsum, s->bias);
     if (cudaGetLastError() != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) { rc = BS3_ERR_CUDA; break; }
   } while (0);
@@ -1142,6 +1160,7 @@ int bs3_solve_batch(bs3_batch_item* items, int64_t n_items, int variant, int acc
         D.q = s->q;
         D.scale = s->scale;
         D.rowsum = s->rowsum;
+        D.bias = s->bias;
         D.par = s->par;
         D.theta_h = s->theta_h;
         D.y0 = s->X;

@@ -34,7 +34,8 @@ constexpr size_t kOffJv64 = align256(kOffJv32 + 6 * kLdMax * sizeof(float));
 constexpr size_t kOffScale = align256(kOffJv64 + 6 * kLdMax * sizeof(double));
 constexpr size_t kOffRowsum = align256(kOffScale + kNoAllocMaxN * sizeof(float));
 constexpr size_t kOffTheta = align256(kOffRowsum + kNoAllocMaxN * sizeof(double));
-constexpr size_t kScratchBytes = align256(kOffTheta + kNoAllocMaxN * sizeof(double));
+constexpr size_t kOffBias = align256(kOffTheta + kNoAllocMaxN * sizeof(double));
+constexpr size_t kScratchBytes = align256(kOffBias + kNoAllocMaxN * sizeof(float));
 
 // Held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -63,28 +64,43 @@ int scratch_address(int device, unsigned char** out) {
 }
 
 // Per-call set-up of the scratch: row scales (1), row sums of the weights
-// (paper-form oscillators), k1/(k0-k1) (circadian) and zeroed j-vectors (their
+// (paper-form oscillators), the rows' biases of the Kuramoto float-float sums
+// (row_bias of sum_j |w_ij|), k1/(k0-k1) (circadian) and zeroed j-vectors (their
 // padding columns multiply zero weights and must not hold stale NaN or Inf).
 // A circadian k1_i outside (0, k0) sets the control block's status to
 // S_INVALID (the check bs3_create_system makes on the host).
 template <typename W>
 __global__ void noalloc_setup(const W* __restrict__ w, int64_t N, int64_t ld, const double* __restrict__ par,
                               int kind, double k0, float* __restrict__ scale, double* __restrict__ rowsum,
-                              double* __restrict__ theta, float* __restrict__ jv32, double* __restrict__ jv64,
-                              Control* __restrict__ ctrl) {
+                              float* __restrict__ bias, double* __restrict__ theta, float* __restrict__ jv32,
+                              double* __restrict__ jv64, Control* __restrict__ ctrl) {
   const int64_t i = blockIdx.x;
-  double acc = 0.0;
-  if (kind == BS3_LCO_PAPER)
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) acc += (double)w[i * ld + j];
-  __shared__ double sm[32];
+  double acc = 0.0, aacc = 0.0;
+  if (kind == BS3_LCO_PAPER || kind == BS3_KURAMOTO)
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      const double v = (double)w[i * ld + j];
+      if (kind == BS3_LCO_PAPER) acc += v;
+      aacc += fabs(v);
+    }
+  __shared__ double sm[32], sa[32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  for (int off = 16; off > 0; off >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    aacc += __shfl_xor_sync(0xffffffffu, aacc, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = acc;
+    sa[threadIdx.x >> 5] = aacc;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double r = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sm[k];
+    double r = 0.0, ra = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      r += sm[k];
+      ra += sa[k];
+    }
     rowsum[i] = r;
+    bias[i] = row_bias(ra);
     scale[i] = 1.0f;
     theta[i] = (kind == BS3_CIRCADIAN) ? par[i] / (k0 - par[i]) : 0.0;
     if (kind == BS3_CIRCADIAN && !(par[i] > 0.0 && par[i] < k0)) atomicCAS(&ctrl->status, 0, (int)S_INVALID);
@@ -142,6 +158,7 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   float* scale = (float*)(base + kOffScale);
   double* rowsum = (double*)(base + kOffRowsum);
   double* theta = (double*)(base + kOffTheta);
+  float* bias = (float*)(base + kOffBias);
   const int d = (kind == BS3_KURAMOTO) ? 1 : (kind == BS3_CIRCADIAN ? 4 : 2);
   const double k0 = (kind == BS3_CIRCADIAN) ? globals[0] : 0.0;
   // paper-form oscillators have no per-agent parameter: any readable array will do
@@ -150,10 +167,10 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   NA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Control), stream));
   if (store == BS3_F64)
     noalloc_setup<double><<<(unsigned)N, 128, 0, stream>>>((const double*)weights, N, ld, par_k, kind, k0, scale,
-                                                           rowsum, theta, jv32, jv64, ctrl);
+                                                           rowsum, bias, theta, jv32, jv64, ctrl);
   else
     noalloc_setup<float><<<(unsigned)N, 128, 0, stream>>>((const float*)weights, N, ld, par_k, kind, k0, scale,
-                                                          rowsum, theta, jv32, jv64, ctrl);
+                                                          rowsum, bias, theta, jv32, jv64, ctrl);
   NA_CUDA(cudaGetLastError());
   if (kind == BS3_CIRCADIAN) {
     // the per-cell check of k1 ran on the device: read its verdict first
@@ -187,6 +204,7 @@ extern "C" int bs3_solve_noalloc(int kind, int64_t N, const double* par, const d
   a.q = weights;
   a.scale = scale;
   a.rowsum = rowsum;
+  a.bias = bias;
   a.par = par_k;
   a.theta_h = theta;
   if (kind == BS3_CIRCADIAN)

@@ -26,6 +26,7 @@ struct Args {
   const void* q;            // [N][ld] stored weights, zero padded
   const float* scale;       // [N] row scales
   const double* rowsum;     // [N] sum_j s_i q_ij (paper-form oscillators)
+  const float* bias;        // [N] row_bias(sum_j |q_ij|): start of the Kuramoto float-float sums
   const double* par;        // [N] omega_i or k1_i
   const double* theta_h;    // [N] k1/(k0-k1) (circadian)
   double g[8];              // circadian k0, k2, k3, a, b, c, eps, I0
@@ -176,13 +177,44 @@ __device__ __forceinline__ void set_packed(Acc<M_SD2>& x, float hi, float lo) { 
 __device__ __forceinline__ void set_packed(Acc<M_SD64>&, float, float) {}
 __device__ __forceinline__ void set_packed(Acc<M_DD>&, float, float) {}
 
+// Bias of a row's Kuramoto float-float sums (see gemv_rows): the power of two
+// B >= 2.5 s for s = sum_j |q_ij| (s computed in binary64; 2.5 covers its
+// rounding and that of q to binary32).  Rows whose sum is not below 1e37 get
+// B = 0, plain binary32 partial sums with approximate error terms.
+__host__ __device__ inline float row_bias(double s) {
+  if (!(s < 1e37)) return 0.0f;
+  if (!(s > 0.0)) return 1.0f;
+  int e = 0;
+  frexp(2.5 * s, &e);   // 2.5 s = f 2^e, f in [0.5, 1)
+  return ldexpf(1.0f, e < -126 ? -126 : e);
+}
+
+// The largest row_bias of rows rb .. rb+nr-1 (0, no bias, when one of them
+// has none); every thread of the CTA calls it and gets the same value.
+__device__ __forceinline__ float cta_bias(const float* bias, int rb, int nr) {
+  __shared__ unsigned s_bits;
+  if (threadIdx.x == 0) s_bits = 0u;
+  __syncthreads();
+  unsigned m = 0u;
+  for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+    const float v = bias[rb + li];
+    const unsigned u = (v > 0.0f) ? __float_as_uint(v) : 0x7f800000u;   // positive floats order as integers
+    m = u > m ? u : m;
+  }
+  if (m) atomicMax(&s_bits, m);
+  __syncthreads();
+  const unsigned b = s_bits;
+  __syncthreads();
+  return b == 0x7f800000u ? 0.0f : (b ? __uint_as_float(b) : 1.0f);
+}
+
 // ---------------------------------------------------------------------------
 // Coupling partial sums of one row block (rows row0 .. row0+nrows-1) for the
 // columns of thread lt of a 128-thread group; then a warp-level reduction.
 // ---------------------------------------------------------------------------
 template <int ST, int MODE, int NV, int RB, bool RES>
 __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int lrow0, int nrows, int lt, int gt,
-                                         const unsigned char* slab, Acc<MODE> (&acc)[RB][NV]) {
+                                         const unsigned char* slab, float cbias, Acc<MODE> (&acc)[RB][NV]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
   constexpr bool DD = (MODE == M_DD);
@@ -195,11 +227,20 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
   const unsigned long long pol = l2_policy(a.l2_keep != 0);
   // Kuramoto with binary32 sums (Sigma = S, or the float-float Sigma = D):
   // the sine and cosine sums of a row advance together in packed f32x2
-  // instructions, lane by lane the scalar operations (same results)
+  // instructions.  The float-float sums start from the CTA's bias B, a power
+  // of two >= 2.5 sum_j |q_ij| for each of its rows: every product
+  // |q_ij v_j| <= |q_ij| (|v_j| <= 1), so the running high part stays in
+  // [B/2, 3B/2], above every product in magnitude, and Fast2Sum (Dekker) gives
+  // each addition's rounding error exactly in three operations instead of
+  // TwoSum's six; hi - B is exact (Sterbenz) at the end.
   constexpr bool PACKED = (NV == 2) && (MODE == M_SS || MODE == M_SD2);
+  const float bias = (PACKED && MODE == M_SD2) ? cbias : 0.0f;
   unsigned long long acc2[RB], lo2[RB];
 #pragma unroll
-  for (int r = 0; r < RB; ++r) acc2[r] = lo2[r] = 0ull;
+  for (int r = 0; r < RB; ++r) {
+    acc2[r] = pk2(bias, bias);
+    lo2[r] = 0ull;
+  }
 #pragma unroll(VEC >= 16 ? 1 : 2)
   for (int col = lt * VEC; col < a.ld; col += gt * VEC) {
     uint4 raw[RB];
@@ -228,13 +269,11 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
             const unsigned long long k2 = pk2(k, k);
             if (MODE == M_SS) {
               acc2[r] = fma2(k2, sc[e], acc2[r]);
-            } else {   // two_sum of (hi, k v), then lo += e, for both sums at once
+            } else {   // fast_two_sum of (hi, k v), then lo += e, for both sums at once
               const unsigned long long p = mul2(k2, sc[e]);
               const unsigned long long sm = add2(acc2[r], p);
-              const unsigned long long bb = sub2(sm, acc2[r]);
-              const unsigned long long er = add2(sub2(acc2[r], sub2(sm, bb)), sub2(p, bb));
+              lo2[r] = add2(lo2[r], sub2(p, sub2(sm, acc2[r])));
               acc2[r] = sm;
-              lo2[r] = add2(lo2[r], er);
             }
           } else {
             float sv0, sv1;
@@ -294,6 +333,10 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
       float a0, a1, l0, l1;
       upk2(acc2[r], a0, a1);
       upk2(lo2[r], l0, l1);
+      if (MODE == M_SD2) {
+        a0 = __fsub_rn(a0, bias);
+        a1 = __fsub_rn(a1, bias);
+      }
       set_packed(acc[r][0], a0, l0);
       set_packed(acc[r][NV - 1], a1, l1);
     }
@@ -538,6 +581,7 @@ struct Ctx {
   double* sth;        // shared k1/(k0-k1)
   double* srs;        // shared row sums
   float* sscale;      // shared row scales
+  float cbias;        // bias of the Kuramoto float-float sums: the largest row_bias of the CTA's rows
   float2* sisc;       // shared binary32 (sin, cos) of each row's last j-vector (Kuramoto), or null
   double2* sisc64;    // shared binary64 (sin, cos) of each row's stage argument (Kuramoto), or null
   bool have64;        // sisc64 holds this stage's values
@@ -779,7 +823,7 @@ __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int bu
     const int nrows = min(RB, x.nr - lrow0);
     Acc<MODE> acc[RB][NV];
     if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, gt, (Acc<MODE>(&)[RB][1])acc);
-    else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, gt, x.slab, acc);
+    else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, gt, x.slab, x.cbias, acc);
     const int wbase = g * wpg;   // first warp of this group
     if (lane == 0) {
 #pragma unroll
@@ -1345,6 +1389,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   float* smlp = a.mlp ? (float*)(dyn + a.smem_mlp_off) : nullptr;
   if (a.mlp)
     for (int k = tid; k < kMlpModel; k += blockDim.x) smlp[k] = a.mlp[k];
+  x.cbias = (KIND == K_KURAMOTO) ? cta_bias(a.bias, x.rb, x.nr) : 0.0f;
   // per-agent parameters and the initial state of this CTA's agents
   for (int li = tid; li < x.nr; li += blockDim.x) {
     const int i = x.rb + li;
@@ -1389,6 +1434,7 @@ struct SysDesc {
   const void* q;
   const float* scale;
   const double* rowsum;
+  const float* bias;
   const double* par;
   const double* theta_h;
   const double* y0;
@@ -1429,6 +1475,7 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   a.q = D.q;
   a.scale = D.scale;
   a.rowsum = D.rowsum;
+  a.bias = D.bias;
   a.par = D.par;
   a.theta_h = D.theta_h;
   a.X = const_cast<double*>(D.y0);
@@ -1461,6 +1508,7 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   x.srs = const_cast<double*>(D.rowsum) + x.rb;
   x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum) + x.rb;   // read only by the circadian kind
   x.sscale = const_cast<float*>(D.scale) + x.rb;
+  x.cbias = (KIND == K_KURAMOTO) ? cta_bias(D.bias, x.rb, x.nr) : 0.0f;
   x.sisc = nullptr;
   x.sisc64 = nullptr;
   x.have64 = false;
