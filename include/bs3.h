@@ -63,9 +63,9 @@ typedef enum { BS3_F64 = 0, BS3_F32 = 1, BS3_BF16 = 2, BS3_F16 = 3, BS3_FP8E4M3 
 /* How a Sigma = D stage sums its binary32 products (G = S):
  * BS3_ACC_F64    each product cast to binary64 and added in binary64 (Sec. 2.3, literal);
  * BS3_ACC_FLOAT2 compensated float-float sum: the exact rounding error of every
- *                addition kept in a binary32 low part (TwoSum; Kuramoto's sums start
- *                from a power-of-two bias >= 2.5 sum_j |q_ij| of every row of a CTA
- *                and take Fast2Sum);
+ *                addition kept in a binary32 low part (TwoSum; the packed sums of the
+ *                Kuramoto and circadian kinds start from a power-of-two bias
+ *                >= 2.5 sum_j |q_ij| of every row of a CTA and take Fast2Sum);
  * BS3_ACC_F32    plain binary32 sum (departs from the table; for study only).
  * Sigma = S stages always sum in binary32; G = D stages in binary64. */
 typedef enum { BS3_ACC_F32 = 0, BS3_ACC_FLOAT2 = 1, BS3_ACC_F64 = 2 } bs3_accum;

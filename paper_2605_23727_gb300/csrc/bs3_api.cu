@@ -177,7 +177,7 @@ __global__ void quantize_kernel(const Src* __restrict__ K, int64_t N, int64_t ld
 }
 
 // rowsum_i = s_i * sum_j q_ij in binary64 (paper-form oscillators) and
-// bias_i = row_bias(sum_j |q_ij|) (the start of the Kuramoto float-float sums).
+// bias_i = row_bias(sum_j |q_ij|) (the start of the packed float-float sums).
 __global__ void rowsum_kernel(const void* __restrict__ q, int st, int64_t N, int64_t ld,
                               const float* __restrict__ s, double* __restrict__ out, float* __restrict__ bias) {
   const int64_t i = blockIdx.x;

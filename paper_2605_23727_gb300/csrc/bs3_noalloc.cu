@@ -64,7 +64,7 @@ int scratch_address(int device, unsigned char** out) {
 }
 
 // Per-call set-up of the scratch: row scales (1), row sums of the weights
-// (paper-form oscillators), the rows' biases of the Kuramoto float-float sums
+// (paper-form oscillators), the rows' biases of the float-float sums
 // (row_bias of sum_j |w_ij|), k1/(k0-k1) (circadian) and zeroed j-vectors (their
 // padding columns multiply zero weights and must not hold stale NaN or Inf).
 // A circadian k1_i outside (0, k0) sets the control block's status to
@@ -76,7 +76,7 @@ __global__ void noalloc_setup(const W* __restrict__ w, int64_t N, int64_t ld, co
                               double* __restrict__ jv64, Control* __restrict__ ctrl) {
   const int64_t i = blockIdx.x;
   double acc = 0.0, aacc = 0.0;
-  if (kind == BS3_LCO_PAPER || kind == BS3_KURAMOTO)
+  if (kind == BS3_LCO_PAPER || kind == BS3_KURAMOTO || kind == BS3_CIRCADIAN)
     for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
       const double v = (double)w[i * ld + j];
       if (kind == BS3_LCO_PAPER) acc += v;

@@ -26,7 +26,7 @@ struct Args {
   const void* q;            // [N][ld] stored weights, zero padded
   const float* scale;       // [N] row scales
   const double* rowsum;     // [N] sum_j s_i q_ij (paper-form oscillators)
-  const float* bias;        // [N] row_bias(sum_j |q_ij|): start of the Kuramoto float-float sums
+  const float* bias;        // [N] row_bias(sum_j |q_ij|): start of the packed float-float sums
   const double* par;        // [N] omega_i or k1_i
   const double* theta_h;    // [N] k1/(k0-k1) (circadian)
   double g[8];              // circadian k0, k2, k3, a, b, c, eps, I0
@@ -177,7 +177,7 @@ __device__ __forceinline__ void set_packed(Acc<M_SD2>& x, float hi, float lo) { 
 __device__ __forceinline__ void set_packed(Acc<M_SD64>&, float, float) {}
 __device__ __forceinline__ void set_packed(Acc<M_DD>&, float, float) {}
 
-// Bias of a row's Kuramoto float-float sums (see gemv_rows): the power of two
+// Bias of a row's packed float-float sums (see gemv_rows and cc_rows): the power of two
 // B >= 2.5 s for s = sum_j |q_ij| (s computed in binary64; 2.5 covers its
 // rounding and that of q to binary32).  Rows whose sum is not below 1e37 get
 // B = 0, plain binary32 partial sums with approximate error terms.
@@ -351,7 +351,7 @@ __device__ __forceinline__ void gemv_rows(const Args& a, int buf, int row0, int 
 
 // Circadian interaction: r_i = sum_j q_ij atan(x_j - x_i) (Eq. CC).
 template <int ST, int MODE, int RB>
-__device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nrows, int lt, int gt,
+__device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nrows, int lt, int gt, float cbias,
                                        Acc<MODE> (&acc)[RB][1]) {
   using L = KLoad<ST>;
   constexpr int VEC = L::VEC;
@@ -371,11 +371,19 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
   }
   // the weight chunks of the next iteration are loaded before the current
   // one's arctangents run, so the stream's latency hides behind them
-  // the float-float sum of a Sigma = D stage runs as a packed TwoSum over the
-  // even and odd columns of each row (two accumulators, merged after the loop)
+  // the float-float sum of a Sigma = D stage runs as a packed Fast2Sum over
+  // the even and odd columns of each row (two accumulators, merged after the
+  // loop), both started from 2B for the CTA's bias B: |arctan| <= pi/2, so
+  // 2B >= 5 sum_j |q_ij| keeps every high part above every product (as in
+  // gemv_rows)
+  constexpr bool PSD2 = (MODE == M_SD2 && VEC <= 8);
+  const float bias = PSD2 ? 2.0f * cbias : 0.0f;
   unsigned long long hi2[RB], lo2[RB];
 #pragma unroll
-  for (int r = 0; r < RB; ++r) hi2[r] = lo2[r] = 0ull;
+  for (int r = 0; r < RB; ++r) {
+    hi2[r] = pk2(bias, bias);
+    lo2[r] = 0ull;
+  }
   uint4 nxt[RB];
   {
     const int col = lt * VEC;
@@ -413,13 +421,11 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
         for (int e = 0; e < VEC; e += 2) {
           float a0, a1;
           atan_f32x2(__fsub_rn(xj[e], xi32[r]), __fsub_rn(xj[e + 1], xi32[r]), a0, a1);
-          if (MODE == M_SD2 && VEC <= 8) {
+          if (PSD2) {
             const unsigned long long pr = mul2(pk2(L::f(raw[r], e), L::f(raw[r], e + 1)), pk2(a0, a1));
             const unsigned long long sm = add2(hi2[r], pr);
-            const unsigned long long bb = sub2(sm, hi2[r]);
-            const unsigned long long er = add2(sub2(hi2[r], sub2(sm, bb)), sub2(pr, bb));
+            lo2[r] = add2(lo2[r], sub2(pr, sub2(sm, hi2[r])));
             hi2[r] = sm;
-            lo2[r] = add2(lo2[r], er);
           } else {
             acc[r][0].add_f(L::f(raw[r], e), a0);
             acc[r][0].add_f(L::f(raw[r], e + 1), a1);
@@ -436,12 +442,14 @@ __device__ __forceinline__ void cc_rows(const Args& a, int buf, int row0, int nr
           acc[r][0].add_d(L::get_d(raw[r], e), atan(__dsub_rn(xj[e], xi64[r])));
     }
   }
-  if (MODE == M_SD2 && VEC <= 8) {
+  if (PSD2) {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       float e0, e1, l0, l1, s_, er;
       upk2(hi2[r], e0, e1);
       upk2(lo2[r], l0, l1);
+      e0 = __fsub_rn(e0, bias);
+      e1 = __fsub_rn(e1, bias);
       two_sum(e0, e1, s_, er);
       set_packed(acc[r][0], s_, __fadd_rn(__fadd_rn(l0, l1), er));
     }
@@ -581,7 +589,7 @@ struct Ctx {
   double* sth;        // shared k1/(k0-k1)
   double* srs;        // shared row sums
   float* sscale;      // shared row scales
-  float cbias;        // bias of the Kuramoto float-float sums: the largest row_bias of the CTA's rows
+  float cbias;        // bias of the float-float sums (Kuramoto, circadian): the largest row_bias of the CTA's rows
   float2* sisc;       // shared binary32 (sin, cos) of each row's last j-vector (Kuramoto), or null
   double2* sisc64;    // shared binary64 (sin, cos) of each row's stage argument (Kuramoto), or null
   bool have64;        // sisc64 holds this stage's values
@@ -822,7 +830,7 @@ __device__ __forceinline__ void stage_m(const Args& a, Ctx& x, int phase, int bu
     const int lrow0 = rbk * RB;
     const int nrows = min(RB, x.nr - lrow0);
     Acc<MODE> acc[RB][NV];
-    if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, gt, (Acc<MODE>(&)[RB][1])acc);
+    if (KIND == K_CIRCADIAN) cc_rows<ST, MODE, RB>(a, buf, x.rb + lrow0, nrows, lt, gt, x.cbias, (Acc<MODE>(&)[RB][1])acc);
     else gemv_rows<ST, MODE, NV, RB, RES>(a, buf, x.rb + lrow0, lrow0, nrows, lt, gt, x.slab, x.cbias, acc);
     const int wbase = g * wpg;   // first warp of this group
     if (lane == 0) {
@@ -1389,7 +1397,7 @@ __global__ void __launch_bounds__(kBlock, 1) bs3_kernel(Args a) {
   float* smlp = a.mlp ? (float*)(dyn + a.smem_mlp_off) : nullptr;
   if (a.mlp)
     for (int k = tid; k < kMlpModel; k += blockDim.x) smlp[k] = a.mlp[k];
-  x.cbias = (KIND == K_KURAMOTO) ? cta_bias(a.bias, x.rb, x.nr) : 0.0f;
+  x.cbias = (KIND == K_KURAMOTO || KIND == K_CIRCADIAN) ? cta_bias(a.bias, x.rb, x.nr) : 0.0f;
   // per-agent parameters and the initial state of this CTA's agents
   for (int li = tid; li < x.nr; li += blockDim.x) {
     const int i = x.rb + li;
@@ -1508,7 +1516,7 @@ __device__ __forceinline__ void batch_job(const BatchArgs& ba, int sidx, int ran
   x.srs = const_cast<double*>(D.rowsum) + x.rb;
   x.sth = const_cast<double*>(D.theta_h ? D.theta_h : D.rowsum) + x.rb;   // read only by the circadian kind
   x.sscale = const_cast<float*>(D.scale) + x.rb;
-  x.cbias = (KIND == K_KURAMOTO) ? cta_bias(D.bias, x.rb, x.nr) : 0.0f;
+  x.cbias = (KIND == K_KURAMOTO || KIND == K_CIRCADIAN) ? cta_bias(D.bias, x.rb, x.nr) : 0.0f;
   x.sisc = nullptr;
   x.sisc64 = nullptr;
   x.have64 = false;

@@ -65,14 +65,16 @@ def rhs_tolerance(osys, y, prec, accum="float2"):
         uS = {"f64": U64, "float2": 2.0 ** -44, "f32": U32}[accum] if G == "S" else U64
     uF = U32 if F == "S" else U64
     coupling_bound = (4 * uG + (N + 64) * uS) * mag
-    if osys.kind == "kuramoto" and S == "D" and G == "S" and accum == "float2":
+    if osys.kind in ("kuramoto", "circadian") and S == "D" and G == "S" and accum == "float2":
         # the packed float-float sums start from the bias B <= 5 sum_j |q_ij| of
-        # the CTA's rows (Fast2Sum): each of the gt >= 32 threads of a row adds
+        # the CTA's rows (circadian: 2B, |arctan| <= pi/2; Fast2Sum): each of
+        # the gt >= 32 threads of a row adds
         # n <= ld/gt + 16 products, and its low part rounds by <= 2^-48 B k at
         # its k-th addition, in all gt n (n + 1) 2^-49 B
         # <= (ld^2/32 + 33 ld + 8192) 2^-49 B
         ld = (N + 15) // 16 * 16
-        coupling_bound = coupling_bound + 5 * (ld * ld / 32 + 33 * ld + 8192) * 2.0 ** -49 * W.sum(axis=1).max()
+        B = (10 if osys.kind == "circadian" else 5) * W.sum(axis=1).max()
+        coupling_bound = coupling_bound + (ld * ld / 32 + 33 * ld + 8192) * 2.0 ** -49 * B
     if osys.kind == "circadian":
         coupling_bound = coupling_bound * 8.0          # pref_i <= k0 a = 4
     Y = np.abs(np.asarray(y, dtype=np.float64).reshape(d, N))
