@@ -75,6 +75,32 @@ def test_rhs_matches_oracle(kind, store, prec, N, resident):
     sysm.close()
 
 
+@pytest.mark.parametrize("kind", ["kuramoto", "circadian"])
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+def test_biased_float_float_sums_with_uneven_rows(kind, store):
+    """The packed float-float sums start from the largest bias of a CTA's rows:
+    a row 1000x heavier than its neighbours loosens their bias, an all-zero
+    row has none of its own; both stay within the stated bound."""
+    bs3 = library()
+    torch = torch_cuda()
+    N = 523
+    w = _workload(kind, N)
+    K = np.array(w.coupling, dtype=np.float64, copy=True)
+    K[17] *= 1000.0
+    K[18] = 0.0
+    K[300] *= 1e-3
+    w.coupling = K.astype(w.coupling.dtype)
+    prec = ("D", "D", "S")
+    sysm = bs3.System.from_workload(w, store)
+    osys = models.from_workload(w, store)
+    got = _gpu_rhs(bs3, torch, sysm, w.y0, prec, "float2")
+    ref = models.rhs(osys, 0.0, w.y0, prec).astype(np.float64)
+    tol = rhs_tolerance(osys, w.y0, prec, "float2")
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (np.flatnonzero(bad)[:5], got[bad][:5], ref[bad][:5], tol[bad][:5])
+    sysm.close()
+
+
 def test_permutation_weights_give_exact_gather():
     """A permutation matrix turns the coupling into a gather: exact in every format."""
     bs3 = library()
